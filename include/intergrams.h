@@ -1,0 +1,166 @@
+/*
+ * intergrams.h - C ABI of the GB300 (sm_103a) top-k n-gram library.
+ *
+ * Problem (paper Sec. 2, Eq. 1 and Eq. 2): given m sequences s_1..s_m over an
+ * alphabet of sigma symbols, n and k, return the k most frequent n-grams
+ * (contiguous length-n windows, never crossing a sequence boundary) with
+ * their counts. Under Eq. 2 (the default) an n-gram counts once per sequence
+ * that contains it; under Eq. 1 every occurrence counts. Ties are broken by
+ * count descending, then by the n-gram's symbols in ascending order.
+ *
+ * Method (paper Sec. 6-7, Algorithm 2 and Algorithm 3): a dense first pass
+ * counts every base_n-gram exactly (base_n = 3 in the paper); its top-Z form
+ * the candidate set P^(base_n). Pass j = base_n+1 .. n counts only the
+ * j-grams whose (j-1)-gram prefix is in P^(j-1), then keeps their top-Z as
+ * P^(j). The answer is the top-k of the last pass. Z is the paper's zk.
+ *
+ * Conventions for every call:
+ *   - No C++ exception crosses this boundary; every call returns ig_status.
+ *     On an error the call also records a message for intergrams_last_error().
+ *   - Work is ordered on the plan's CUDA stream. A plan is not thread-safe;
+ *     distinct plans are independent and may be used from different threads.
+ *   - All counts are exact integers. The GPU path is deterministic: the same
+ *     inputs and parameters give byte-identical results regardless of the
+ *     tuning choices.
+ */
+#ifndef INTERGRAMS_H
+#define INTERGRAMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IG_OK = 0,
+  IG_DONE = 1,            /* intergrams_pass: every pass has already run */
+  IG_EINVAL = -1,         /* invalid argument or unsupported parameter combination */
+  IG_ENOMEM = -2,         /* device or host allocation failed */
+  IG_ETABLE_FULL = -3,    /* a device hash table ran out of room (internal limit) */
+  IG_EOVERFLOW = -4,      /* a 32-bit device count overflowed (Eq. 1 on > 2^32-1 windows) */
+  IG_ETIMEOUT = -5,       /* a bounded device-side wait gave up */
+  IG_ECUDA = -6,          /* a CUDA runtime call failed; see intergrams_last_error() */
+  IG_ESTATE = -7          /* call out of order (e.g. topk before any pass) */
+} ig_status;
+
+/* count_mode */
+#define IG_COUNT_ONCE_PER_SEQUENCE 0u   /* Eq. 2 (paper's focus, default) */
+#define IG_COUNT_EVERY_OCCURRENCE  1u   /* Eq. 1 */
+
+/* flags */
+#define IG_F_HOST_INPUT (1u << 0)  /* data/offsets are HOST pointers: the plan copies
+                                      them to device memory it owns (stream-ordered) */
+#define IG_F_GRAPH      (1u << 1)  /* capture each pass's launch sequence as a CUDA
+                                      graph on first use and replay it afterwards */
+#define IG_F_AUTOTUNE   (1u << 2)  /* let the autotuner pick the tuning knobs left at 0 */
+
+typedef struct {
+  uint32_t n;            /* target n-gram length in symbols: 1..64 (bytes), 1..32 (2-bit) */
+  uint32_t k;            /* number of results wanted, >= 1 */
+  uint32_t candidates;   /* Z: size of each intermediate candidate set P^(j); k <= Z < 2^24 */
+  uint32_t base_n;       /* length of the dense first pass: 1..3 (bytes), 1..12 (2-bit);
+                            the paper uses 3. Passes run for j = min(base_n, n) .. n */
+  uint32_t symbol_bits;  /* 8: one symbol per byte; 2: bases A,C,G,T = 0..3 packed four per
+                            byte, most significant bits first, sequences at any base offset */
+  uint32_t count_mode;   /* IG_COUNT_ONCE_PER_SEQUENCE or IG_COUNT_EVERY_OCCURRENCE */
+  uint32_t flags;        /* IG_F_* */
+} ig_params;
+
+/* Tuning knobs. A zero field means "default" (or "autotune" with IG_F_AUTOTUNE).
+ * No knob changes any result; they only change speed and memory. */
+typedef struct {
+  uint32_t ctas_per_sm;      /* persistent scan CTAs per SM (1..4) */
+  uint32_t threads;          /* threads per scan CTA (256, 512 or 1024) */
+  uint32_t words_per_thread; /* 32-bit smem words of symbols each thread scans per tile (odd, 1..31) */
+  uint32_t smem_set_log2;    /* log2 entries of the per-sequence shared-memory dedupe set (8..15) */
+  uint32_t table_load_pct;   /* maximum load of the candidate probe table, percent (10..50) */
+  uint32_t hot_log2;         /* log2 entries of the shared-memory hot candidate cache (0 = off, 6..12) */
+} ig_tuning;
+
+typedef struct ig_plan ig_plan;
+
+/*
+ * intergrams_plan - validate the inputs and build a plan for one corpus.
+ *   p        : parameters (copied).
+ *   data     : the concatenated sequences (device pointer; host pointer with
+ *              IG_F_HOST_INPUT). Bytes for symbol_bits 8; packed bases for 2.
+ *              Caller-owned; must stay valid and unchanged until
+ *              intergrams_free unless IG_F_HOST_INPUT is set.
+ *   offsets  : uint64[m + 1] sequence boundaries in symbols; offsets[0] = 0,
+ *              non-decreasing; offsets[m] = total symbols. Same ownership
+ *              rules as data. Sequence i is symbols [offsets[i], offsets[i+1]).
+ *   m        : number of sequences (0 is allowed: every result is empty).
+ *   stream   : cudaStream_t the plan's work is ordered on (NULL = legacy default).
+ *   tuning   : optional knobs (NULL = defaults).
+ *   out      : receives the plan. The plan owns every table it allocates.
+ * Reads offsets to the host once (one small D2H copy) to schedule work.
+ * Errors: IG_EINVAL (bad parameters or offsets), IG_ENOMEM, IG_ECUDA.
+ */
+ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* offsets,
+                          uint32_t m, void* stream, const ig_tuning* tuning, ig_plan** out);
+
+/*
+ * intergrams_pass - run the next pass (the dense base pass first, then the
+ * candidate passes j = base_n+1 .. n, paper Algorithm 3) and its selection.
+ *   j_done : receives the n-gram length j of the pass just run.
+ * Returns IG_OK, or IG_DONE (nothing run) once pass n has completed.
+ * Synchronises the plan's stream once to read the device status word.
+ */
+ig_status intergrams_pass(ig_plan* pl, uint32_t* j_done);
+
+/*
+ * intergrams_run - run every remaining pass (equivalent to calling
+ * intergrams_pass until it returns IG_DONE, with one status read at the end).
+ */
+ig_status intergrams_run(ig_plan* pl);
+
+/*
+ * intergrams_rewind - return the plan to its state before the first pass so
+ * the whole job can run again over the same corpus buffers (whose contents
+ * may have changed, as long as the offsets did not). Tables are reused; with
+ * IG_F_GRAPH a graph captured by intergrams_run is replayed. Stream-ordered,
+ * no synchronisation.
+ */
+ig_status intergrams_rewind(ig_plan* pl);
+
+/*
+ * intergrams_topk - the top-k j-grams of the latest completed pass j (paper
+ * Algorithm 3, final k-argmax; after pass j < n this is the top-k of that
+ * intermediate pass).
+ *   keys_out   : HOST buffer of capacity * ceil(j * symbol_bits / 8) bytes; row r is
+ *                the r-th n-gram, symbols in order, packed like the input
+ *                (2-bit symbols most significant first, zero padded). May be NULL.
+ *   counts_out : HOST buffer of capacity uint64 counts. May be NULL.
+ *   capacity   : rows the buffers hold; min(k, capacity, #nonzero) rows are written.
+ *   k_out      : receives the number of rows written.
+ *   j_out      : optional; receives j (the length of each returned n-gram).
+ * Rows are ordered by count descending, then symbols ascending.
+ * Errors: IG_ESTATE if no pass has run yet.
+ */
+ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out,
+                          uint32_t capacity, uint32_t* k_out, uint32_t* j_out);
+
+/* Per-pass statistics of the latest pass (device counters, read on demand). */
+typedef struct {
+  uint32_t j;               /* n-gram length of the pass */
+  uint64_t windows;         /* windows in the corpus for this j */
+  uint64_t survivors;       /* windows whose (j-1)-prefix was a candidate (all, for the base pass) */
+  uint64_t registrations;   /* count increments issued (Eq. 2: distinct (sequence, j-gram) pairs) */
+  uint64_t nonzero_selected;/* size of the selected set (<= Z, or <= k at the last pass) */
+  uint64_t scanned_bytes;   /* bytes of corpus streamed by the scan */
+} ig_pass_stats;
+
+ig_status intergrams_stats(ig_plan* pl, ig_pass_stats* out);
+
+/* Release every resource of the plan (stream-ordered frees). NULL is ignored. */
+void intergrams_free(ig_plan* pl);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* intergrams_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INTERGRAMS_H */

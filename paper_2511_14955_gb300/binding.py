@@ -1,0 +1,193 @@
+"""Thin ctypes binding of ``libintergrams.so`` (argument marshalling only).
+
+Every step of the computation runs in the library's sm_103a kernels; this
+module only converts arguments. PyTorch supplies device memory and streams.
+If the library is missing the import of :class:`Plan` fails loudly - there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from . import _build
+
+IG_OK, IG_DONE = 0, 1
+STATUS_NAMES = {0: "IG_OK", 1: "IG_DONE", -1: "IG_EINVAL", -2: "IG_ENOMEM", -3: "IG_ETABLE_FULL",
+                -4: "IG_EOVERFLOW", -5: "IG_ETIMEOUT", -6: "IG_ECUDA", -7: "IG_ESTATE"}
+COUNT_ONCE_PER_SEQUENCE = 0
+COUNT_EVERY_OCCURRENCE = 1
+F_HOST_INPUT = 1 << 0
+F_GRAPH = 1 << 1
+F_AUTOTUNE = 1 << 2
+
+# every symbol include/intergrams.h declares
+EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_rewind", "intergrams_topk",
+           "intergrams_stats", "intergrams_free", "intergrams_last_error"]
+
+
+class IgParams(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in
+                ("n", "k", "candidates", "base_n", "symbol_bits", "count_mode", "flags")]
+
+
+class IgTuning(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in
+                ("ctas_per_sm", "threads", "words_per_thread", "smem_set_log2", "table_load_pct", "hot_log2")]
+
+
+class IgPassStats(ctypes.Structure):
+    _fields_ = [("j", ctypes.c_uint32), ("windows", ctypes.c_uint64), ("survivors", ctypes.c_uint64),
+                ("registrations", ctypes.c_uint64), ("nonzero_selected", ctypes.c_uint64),
+                ("scanned_bytes", ctypes.c_uint64)]
+
+
+class IntergramsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> Path:
+    return _build.LIB / "libintergrams.so"
+
+
+def load(build_if_missing: bool = True):
+    """Load the native library (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if build_if_missing:
+        path = _build.build_cuda()
+    if not path.exists():
+        raise RuntimeError(f"{path} is missing: the CUDA library must be built (no CPU fallback)")
+    lib = ctypes.CDLL(str(path))
+    P, U32 = ctypes.c_void_p, ctypes.c_uint32
+    lib.intergrams_plan.restype = ctypes.c_int
+    lib.intergrams_plan.argtypes = [ctypes.POINTER(IgParams), P, P, U32, P, ctypes.POINTER(IgTuning),
+                                    ctypes.POINTER(ctypes.c_void_p)]
+    lib.intergrams_pass.restype = ctypes.c_int
+    lib.intergrams_pass.argtypes = [P, ctypes.POINTER(U32)]
+    lib.intergrams_run.restype = ctypes.c_int
+    lib.intergrams_run.argtypes = [P]
+    lib.intergrams_rewind.restype = ctypes.c_int
+    lib.intergrams_rewind.argtypes = [P]
+    lib.intergrams_topk.restype = ctypes.c_int
+    lib.intergrams_topk.argtypes = [P, P, P, U32, ctypes.POINTER(U32), ctypes.POINTER(U32)]
+    lib.intergrams_stats.restype = ctypes.c_int
+    lib.intergrams_stats.argtypes = [P, ctypes.POINTER(IgPassStats)]
+    lib.intergrams_free.restype = None
+    lib.intergrams_free.argtypes = [P]
+    lib.intergrams_last_error.restype = ctypes.c_char_p
+    lib.intergrams_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(lib, st: int, what: str):
+    if st not in (IG_OK, IG_DONE):
+        raise IntergramsError(st, f"{what}: {lib.intergrams_last_error().decode(errors='replace')}")
+    return st
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return np.ascontiguousarray(x).ctypes.data
+
+
+class Plan:
+    """One top-k n-gram job over a corpus (see include/intergrams.h).
+
+    ``data``/``offsets`` are CUDA tensors (uint8 / int64 holding uint64
+    boundaries) unless ``host_input`` is set, in which case they are numpy
+    arrays and the library copies them to the device itself.
+    """
+
+    def __init__(self, data, offsets, *, n: int, k: int, candidates: int, base_n: int = 3,
+                 symbol_bits: int = 8, count_mode: int = COUNT_ONCE_PER_SEQUENCE, graph: bool = False,
+                 host_input: bool = False, stream=None, tuning: dict | None = None):
+        self._lib = load()
+        self._h = ctypes.c_void_p(None)
+        flags = (F_GRAPH if graph else 0) | (F_HOST_INPUT if host_input else 0)
+        self.params = IgParams(n, k, candidates, base_n, symbol_bits, count_mode, flags)
+        tun = IgTuning(**(tuning or {}))
+        if host_input:
+            self._keep = (np.ascontiguousarray(data, dtype=np.uint8),
+                          np.ascontiguousarray(offsets, dtype=np.uint64))
+        else:
+            self._keep = (data, offsets)
+        m = len(offsets) - 1
+        if stream is None:
+            stream_ptr = None
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream_ptr = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                pass
+        else:
+            stream_ptr = getattr(stream, "cuda_stream", stream)
+        _check(self._lib, self._lib.intergrams_plan(ctypes.byref(self.params), _ptr(self._keep[0]),
+                                                    _ptr(self._keep[1]), m, stream_ptr,
+                                                    ctypes.byref(tun), ctypes.byref(self._h)),
+               "intergrams_plan")
+        self.n = n
+        self.symbol_bits = symbol_bits
+
+    def step(self):
+        """Run the next pass; returns its j, or None when every pass has run."""
+        j = ctypes.c_uint32(0)
+        st = _check(self._lib, self._lib.intergrams_pass(self._h, ctypes.byref(j)), "intergrams_pass")
+        return None if st == IG_DONE else j.value
+
+    def run(self):
+        _check(self._lib, self._lib.intergrams_run(self._h), "intergrams_run")
+
+    def rewind(self):
+        _check(self._lib, self._lib.intergrams_rewind(self._h), "intergrams_rewind")
+
+    def topk(self, capacity: int | None = None):
+        """(keys, counts, j): keys is a (rows, ceil(j*bits/8)) uint8 array."""
+        cap = self.params.k if capacity is None else int(capacity)
+        row = (self.n * self.symbol_bits + 7) // 8
+        keys = np.zeros((max(cap, 1), row), np.uint8)
+        counts = np.zeros(max(cap, 1), np.uint64)
+        kout, jout = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        _check(self._lib, self._lib.intergrams_topk(self._h, keys.ctypes.data, counts.ctypes.data, cap,
+                                                    ctypes.byref(kout), ctypes.byref(jout)), "intergrams_topk")
+        r, j = kout.value, jout.value
+        rb = (j * self.symbol_bits + 7) // 8
+        flat = keys.reshape(-1)[: r * rb].reshape(r, rb) if r else np.zeros((0, rb), np.uint8)
+        return flat.copy(), counts[:r].copy(), j
+
+    def stats(self) -> dict:
+        s = IgPassStats()
+        _check(self._lib, self._lib.intergrams_stats(self._h, ctypes.byref(s)), "intergrams_stats")
+        return {f: getattr(s, f) for f, _ in IgPassStats._fields_}
+
+    def close(self):
+        if self._h and self._h.value:
+            self._lib.intergrams_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

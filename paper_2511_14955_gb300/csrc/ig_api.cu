@@ -1,0 +1,459 @@
+// C ABI of the top-k n-gram library: plan / pass / run / topk / stats / free.
+//
+// A plan owns every device table of one job. Pass j (paper Algorithm 3):
+//   reset queue + epochs -> zero the slot counters -> scan the corpus ->
+//   select top-Z (top-k at the last pass) -> if j < n, build P^(j).
+// All sizes the kernels need are kept on the device, so the launch sequence
+// of a pass is fixed; with IG_F_GRAPH the whole remaining pass sequence is
+// captured once as a CUDA graph and replayed by later runs of the same plan.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ig_internal.cuh"
+
+using namespace ig;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ig_status fail(ig_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define IG_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? IG_ENOMEM : IG_ECUDA,                      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    }                                                                                          \
+  } while (0)
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+}  // namespace
+
+struct ig_plan {
+  ig_params p{};
+  ig_tuning t{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+
+  const uint8_t* data = nullptr;
+  uint64_t data_bytes = 0;
+  const uint64_t* offsets = nullptr;
+  uint32_t m = 0;
+  uint8_t* own_data = nullptr;
+  uint64_t* own_offsets = nullptr;
+  std::vector<uint64_t> h_offsets;
+  uint64_t total_syms = 0, max_len = 0;
+
+  uint32_t sigma = 256, sb = 8;
+  uint32_t b = 3;          // length of the first (dense) pass
+  uint32_t next_j = 0;     // next pass to run
+  uint32_t last_j = 0;     // last completed pass (0 = none)
+  uint32_t nsel_last = 0;  // size of the latest selection
+
+  uint64_t nslots_base = 0, nslots_cand = 0;
+  uint32_t* counts = nullptr;
+  uint4* table = nullptr;
+  uint32_t table_log2 = 0;
+  unsigned long long* keys[2] = {nullptr, nullptr};
+  int cur = 0;             // keys[cur] = keys of the latest candidate set
+  uint32_t* sel_slot = nullptr;
+  uint32_t* sel_count = nullptr;
+  uint32_t* hist = nullptr;
+  uint32_t* blk = nullptr;
+  int G = 1024;
+  uint32_t *sidx[2] = {nullptr, nullptr}, *skey[2] = {nullptr, nullptr}, *shist = nullptr;
+  uint32_t sort_cap = 0;
+  unsigned long long* gset = nullptr;
+  uint32_t gset_log2 = 1;
+  uint64_t gset_entries = 0;
+  PassCtl* ctl = nullptr;
+  PassCtl* h_ctl = nullptr;  // pinned mirror for status reads
+  uint32_t* d_order = nullptr;
+
+  int scan_grid = 0, scan_threads = 512;
+  size_t scan_smem = 0;
+  uint32_t tile_words = 0;
+
+  uint8_t* out_keys = nullptr;
+  unsigned long long* out_counts = nullptr;
+  uint32_t out_cap = 0;
+
+  cudaGraphExec_t graph = nullptr;  // full job from the first pass (IG_F_GRAPH)
+  cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
+  bool check_overflow = false;
+};
+
+namespace {
+
+uint32_t row_bytes_for(const ig_plan* pl, uint32_t j) { return (j * pl->sb + 7) / 8; }
+
+uint64_t windows_for(const ig_plan* pl, uint32_t j) {
+  uint64_t w = 0;
+  for (uint32_t i = 0; i < pl->m; ++i) {
+    uint64_t L = pl->h_offsets[i + 1] - pl->h_offsets[i];
+    if (L >= j) w += L - j + 1;
+  }
+  return w;
+}
+
+void release(ig_plan* pl) {
+  if (!pl) return;
+  if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  void* ptrs[] = {pl->own_data, pl->own_offsets, pl->counts, pl->table, pl->keys[0], pl->keys[1],
+                  pl->sel_slot, pl->sel_count, pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
+                  pl->skey[1], pl->shist, pl->gset, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
+  delete pl;
+}
+
+// Enqueue pass j (no host synchronisation).
+void enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
+  const bool base = (j == pl->b);
+  const uint64_t ns = base ? pl->nslots_base : pl->nslots_cand;
+  launch_pass_reset(pl->ctl, pl->m, pl->p.count_mode == IG_COUNT_ONCE_PER_SEQUENCE ? pl->gset : nullptr,
+                    pl->gset_entries, s);
+  cudaMemsetAsync(pl->counts, 0, ns * sizeof(uint32_t), s);
+  ScanArgs a{};
+  a.data = pl->data;
+  a.data_bytes = pl->data_bytes;
+  a.offsets = pl->offsets;
+  a.order = pl->d_order;
+  a.m = pl->m;
+  a.j = j;
+  a.key_mask = (j * pl->sb >= 64) ? ~0ull : ((1ull << (j * pl->sb)) - 1ull);
+  a.table = base ? nullptr : pl->table;
+  a.table_log2 = pl->table_log2;
+  a.counts = pl->counts;
+  a.gset = pl->gset;
+  a.gset_log2 = pl->gset_log2;
+  a.count_mode = pl->p.count_mode;
+  a.words_per_thread = pl->t.words_per_thread;
+  a.sset_log2 = pl->t.smem_set_log2;
+  a.tile_words = pl->tile_words;
+  a.check_overflow = pl->check_overflow ? 1u : 0u;
+  a.ctl = pl->ctl;
+  if (pl->m > 0) launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
+  const uint32_t target = (j < pl->p.n) ? pl->p.candidates : pl->p.k;
+  launch_select(pl->counts, ns, target, pl->ctl, pl->hist, pl->blk, pl->G, pl->sel_slot, pl->sel_count, s);
+  if (j < pl->p.n) {
+    const int nxt = pl->cur ^ 1;
+    launch_build_candidates(pl->sel_slot, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], pl->table,
+                            pl->table_log2, s);
+  }
+}
+
+// After pass j has been enqueued: bookkeeping on the host.
+void finish_pass_host(ig_plan* pl, uint32_t j) {
+  if (j < pl->p.n) pl->cur ^= 1;
+  pl->last_j = j;
+  pl->next_j = j + 1;
+}
+
+ig_status read_status(ig_plan* pl) {
+  IG_CUDA(cudaMemcpyAsync(pl->h_ctl, pl->ctl, sizeof(PassCtl), cudaMemcpyDeviceToHost, pl->stream));
+  IG_CUDA(cudaStreamSynchronize(pl->stream));
+  IG_CUDA(cudaGetLastError());
+  const uint32_t st = pl->h_ctl->status;
+  pl->nsel_last = pl->h_ctl->nsel;
+  if (st & kStCountOverflow) return fail(IG_EOVERFLOW, "a 32-bit count overflowed");
+  if (st & (kStSetFull | kStTableFull)) return fail(IG_ETABLE_FULL, "a device hash table filled up");
+  if (st) return fail(IG_ECUDA, "device status error");
+  return IG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* intergrams_last_error(void) { return g_last_error.c_str(); }
+
+ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* offsets, uint32_t m, void* stream,
+                          const ig_tuning* tuning, ig_plan** out) {
+  g_last_error.clear();
+  if (!out) return fail(IG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(IG_EINVAL, "params is NULL");
+  if (p->symbol_bits != 8 && p->symbol_bits != 2) return fail(IG_EINVAL, "symbol_bits must be 8 or 2");
+  const uint32_t max_n = p->symbol_bits == 8 ? 8u : 32u;
+  if (p->n < 1 || p->n > max_n)
+    return fail(IG_EINVAL, "n out of range (this build supports n <= 8 bytes or n <= 32 bases)");
+  if (p->k < 1) return fail(IG_EINVAL, "k must be >= 1");
+  if (p->candidates < p->k || p->candidates >= (1u << 24)) return fail(IG_EINVAL, "need k <= candidates < 2^24");
+  const uint32_t max_base = p->symbol_bits == 8 ? 3u : 12u;
+  if (p->base_n < 1 || p->base_n > max_base) return fail(IG_EINVAL, "base_n out of range");
+  if (p->count_mode > 1) return fail(IG_EINVAL, "count_mode must be 0 or 1");
+  if (!offsets) return fail(IG_EINVAL, "offsets is NULL");
+
+  ig_plan* pl = new (std::nothrow) ig_plan();
+  if (!pl) return fail(IG_ENOMEM, "host allocation failed");
+  pl->p = *p;
+  pl->stream = reinterpret_cast<cudaStream_t>(stream);
+  pl->m = m;
+  pl->sb = p->symbol_bits;
+  pl->sigma = 1u << pl->sb;
+  pl->b = std::min(p->base_n, p->n);
+  pl->next_j = pl->b;
+
+  auto bail = [&](ig_status st) {
+    release(pl);
+    return st;
+  };
+#define PLAN_CUDA(call)                                                                              \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return bail(fail(e_ == cudaErrorMemoryAllocation ? IG_ENOMEM : IG_ECUDA,                       \
+                       std::string(#call) + ": " + cudaGetErrorString(e_)));                        \
+  } while (0)
+
+  PLAN_CUDA(cudaGetDevice(&pl->device));
+  PLAN_CUDA(cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, pl->device));
+
+  // offsets on the host
+  pl->h_offsets.resize((size_t)m + 1);
+  if (p->flags & IG_F_HOST_INPUT) {
+    std::memcpy(pl->h_offsets.data(), offsets, sizeof(uint64_t) * ((size_t)m + 1));
+  } else {
+    PLAN_CUDA(cudaMemcpyAsync(pl->h_offsets.data(), offsets, sizeof(uint64_t) * ((size_t)m + 1),
+                              cudaMemcpyDeviceToHost, pl->stream));
+    PLAN_CUDA(cudaStreamSynchronize(pl->stream));
+  }
+  if (pl->h_offsets[0] != 0) return bail(fail(IG_EINVAL, "offsets[0] must be 0"));
+  for (uint32_t i = 0; i < m; ++i) {
+    if (pl->h_offsets[i + 1] < pl->h_offsets[i]) return bail(fail(IG_EINVAL, "offsets must be non-decreasing"));
+    pl->max_len = std::max(pl->max_len, pl->h_offsets[i + 1] - pl->h_offsets[i]);
+  }
+  pl->total_syms = pl->h_offsets[m];
+  pl->data_bytes = (pl->total_syms * pl->sb + 7) / 8;
+  if (pl->data_bytes && !data) return bail(fail(IG_EINVAL, "data is NULL"));
+
+  if (p->flags & IG_F_HOST_INPUT) {
+    PLAN_CUDA(dev_alloc(&pl->own_data, pl->data_bytes));
+    PLAN_CUDA(dev_alloc(&pl->own_offsets, (size_t)m + 1));
+    if (pl->data_bytes)
+      PLAN_CUDA(cudaMemcpyAsync(pl->own_data, data, pl->data_bytes, cudaMemcpyHostToDevice, pl->stream));
+    PLAN_CUDA(cudaMemcpyAsync(pl->own_offsets, pl->h_offsets.data(), sizeof(uint64_t) * ((size_t)m + 1),
+                              cudaMemcpyHostToDevice, pl->stream));
+    pl->data = pl->own_data;
+    pl->offsets = pl->own_offsets;
+  } else {
+    pl->data = reinterpret_cast<const uint8_t*>(data);
+    pl->offsets = offsets;
+  }
+
+  // tuning (defaults; the autotuner in the binding may override)
+  ig_tuning t{};
+  if (tuning) t = *tuning;
+  if (!t.ctas_per_sm) t.ctas_per_sm = 2;
+  if (!t.threads) t.threads = 512;
+  if (!t.words_per_thread) t.words_per_thread = 9;
+  if (!t.smem_set_log2) t.smem_set_log2 = 14;
+  if (!t.table_load_pct) t.table_load_pct = 25;
+  if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
+      !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
+      t.table_load_pct < 10 || t.table_load_pct > 50)
+    return bail(fail(IG_EINVAL, "tuning knob out of range"));
+  pl->t = t;
+
+  // sizes
+  uint64_t nb = 1;
+  for (uint32_t i = 0; i < pl->b; ++i) nb *= pl->sigma;
+  pl->nslots_base = nb;
+  pl->nslots_cand = (pl->b < p->n) ? (uint64_t)pl->sigma * p->candidates : 0;
+  const uint64_t nslots = std::max(pl->nslots_base, pl->nslots_cand);
+  pl->table_log2 = ceil_log2_u64((uint64_t)p->candidates * 100 / t.table_load_pct + 1);
+  if (pl->table_log2 < 4) pl->table_log2 = 4;
+  pl->sort_cap = p->candidates;
+  const uint32_t sortG = (pl->sort_cap + kSortChunk - 1) / kSortChunk;
+
+  // Eq. 1 with 2^32 or more windows can overflow a 32-bit count
+  pl->check_overflow = p->count_mode == IG_COUNT_EVERY_OCCURRENCE && pl->total_syms >= 0xFFFFFFFFull;
+
+  // scan launch geometry
+  const uint32_t spw = 32 / pl->sb;
+  const uint64_t tile_syms = (uint64_t)t.words_per_thread * spw * t.threads + p->n + 2 * 16 * (8 / pl->sb);
+  pl->tile_words = (uint32_t)((tile_syms * pl->sb + 31) / 32) + 8;
+  pl->tile_words = (pl->tile_words + 3) & ~3u;
+  pl->scan_threads = (int)t.threads;
+  pl->scan_smem = ((size_t)4 << t.smem_set_log2) + (size_t)pl->tile_words * 4;
+  for (bool base : {true, false}) PLAN_CUDA(scan_set_smem_limit(pl->sb, base, pl->scan_smem));
+  int occ = std::min(scan_max_ctas_per_sm(pl->sb, false, pl->scan_threads, pl->scan_smem),
+                     scan_max_ctas_per_sm(pl->sb, true, pl->scan_threads, pl->scan_smem));
+  if (occ < 1) return bail(fail(IG_EINVAL, "scan kernel does not fit on an SM with these tuning knobs"));
+  pl->scan_grid = pl->sms * (int)std::min<uint32_t>(t.ctas_per_sm, (uint32_t)occ);
+
+  // Eq. 2 dedupe sets: one per scan CTA, sized for the longest sequence
+  if (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+    pl->gset_log2 = ceil_log2_u64(2 * std::max<uint64_t>(pl->max_len, 1));
+    pl->gset_log2 = std::max<uint32_t>(pl->gset_log2, 5);
+    pl->gset_log2 = std::min<uint32_t>(pl->gset_log2, 24);
+    pl->gset_entries = (uint64_t)pl->scan_grid << pl->gset_log2;
+  } else {
+    pl->gset_log2 = 1;
+    pl->gset_entries = 2;
+  }
+
+  PLAN_CUDA(dev_alloc(&pl->counts, nslots));
+  PLAN_CUDA(dev_alloc(&pl->table, (size_t)1 << pl->table_log2));
+  PLAN_CUDA(dev_alloc(&pl->keys[0], p->candidates));
+  PLAN_CUDA(dev_alloc(&pl->keys[1], p->candidates));
+  PLAN_CUDA(dev_alloc(&pl->sel_slot, p->candidates));
+  PLAN_CUDA(dev_alloc(&pl->sel_count, p->candidates));
+  PLAN_CUDA(dev_alloc(&pl->hist, (size_t)kMaxLevels * kHistBins));
+  PLAN_CUDA(dev_alloc(&pl->blk, (size_t)2 * pl->G));
+  PLAN_CUDA(dev_alloc(&pl->sidx[0], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(&pl->sidx[1], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(&pl->skey[0], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(&pl->skey[1], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(&pl->shist, (size_t)kSortDigits * sortG));
+  PLAN_CUDA(dev_alloc(&pl->gset, pl->gset_entries));
+  PLAN_CUDA(cudaMemsetAsync(pl->gset, 0, pl->gset_entries * sizeof(unsigned long long), pl->stream));
+  PLAN_CUDA(dev_alloc(&pl->ctl, 1));
+  PLAN_CUDA(cudaMemsetAsync(pl->ctl, 0, sizeof(PassCtl), pl->stream));
+  PLAN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&pl->h_ctl), sizeof(PassCtl)));
+  pl->out_cap = p->k;
+  PLAN_CUDA(dev_alloc(&pl->out_keys, (size_t)pl->out_cap * row_bytes_for(pl, p->n) + 8));
+  PLAN_CUDA(dev_alloc(&pl->out_counts, pl->out_cap));
+
+  // schedule: sequences longest first (ties by index)
+  std::vector<uint32_t> order(m);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    return pl->h_offsets[x + 1] - pl->h_offsets[x] > pl->h_offsets[y + 1] - pl->h_offsets[y];
+  });
+  PLAN_CUDA(dev_alloc(&pl->d_order, m));
+  if (m) PLAN_CUDA(cudaMemcpyAsync(pl->d_order, order.data(), sizeof(uint32_t) * m, cudaMemcpyHostToDevice, pl->stream));
+  PLAN_CUDA(cudaStreamSynchronize(pl->stream));
+#undef PLAN_CUDA
+  *out = pl;
+  return IG_OK;
+}
+
+ig_status intergrams_pass(ig_plan* pl, uint32_t* j_done) {
+  g_last_error.clear();
+  if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  if (pl->next_j > pl->p.n) return IG_DONE;
+  const uint32_t j = pl->next_j;
+  enqueue_pass(pl, j, pl->stream);
+  IG_CUDA(cudaGetLastError());
+  finish_pass_host(pl, j);
+  if (j_done) *j_done = j;
+  return read_status(pl);
+}
+
+ig_status intergrams_run(ig_plan* pl) {
+  g_last_error.clear();
+  if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  if (pl->next_j > pl->p.n) return IG_OK;
+  const bool from_start = pl->next_j == pl->b;
+  if ((pl->p.flags & IG_F_GRAPH) && from_start) {
+    if (!pl->graph) {
+      // capture on a private stream (the legacy default stream cannot be
+      // captured); the graph is then launched on the plan's stream
+      cudaGraph_t g = nullptr;
+      if (!pl->cap_stream) IG_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+      IG_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int cur0 = pl->cur;
+      for (uint32_t j = pl->b; j <= pl->p.n; ++j) {
+        enqueue_pass(pl, j, pl->cap_stream);
+        if (j < pl->p.n) pl->cur ^= 1;
+      }
+      pl->cur = cur0;
+      cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+      if (e != cudaSuccess) return fail(IG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&pl->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(IG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    IG_CUDA(cudaGraphLaunch(pl->graph, pl->stream));
+    for (uint32_t j = pl->b; j <= pl->p.n; ++j) finish_pass_host(pl, j);
+    return read_status(pl);
+  }
+  for (uint32_t j = pl->next_j; j <= pl->p.n; ++j) {
+    enqueue_pass(pl, j, pl->stream);
+    finish_pass_host(pl, j);
+  }
+  IG_CUDA(cudaGetLastError());
+  return read_status(pl);
+}
+
+ig_status intergrams_rewind(ig_plan* pl) {
+  g_last_error.clear();
+  if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  pl->cur = 0;  // the key buffers' parity at the start of a run (graphs are captured with it)
+  pl->next_j = pl->b;
+  pl->last_j = 0;
+  pl->nsel_last = 0;
+  return IG_OK;
+}
+
+ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out, uint32_t capacity, uint32_t* k_out,
+                          uint32_t* j_out) {
+  g_last_error.clear();
+  if (!pl || !k_out) return fail(IG_EINVAL, "plan or k_out is NULL");
+  *k_out = 0;
+  if (pl->last_j == 0) return fail(IG_ESTATE, "no pass has run yet");
+  const uint32_t j = pl->last_j;
+  if (j_out) *j_out = j;
+  const uint32_t rows = std::min(std::min(pl->p.k, capacity), pl->nsel_last);
+  if (rows == 0) return IG_OK;
+  cudaStream_t s = pl->stream;
+  launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
+                       pl->shist, s);
+  // keys of the selected j-grams: parent keys are P^(j-1) (for j < n the
+  // buffers were flipped after P^(j) was built, so P^(j-1) is keys[cur^1])
+  const bool base = (j == pl->b);
+  const unsigned long long* prev = (j < pl->p.n) ? pl->keys[pl->cur ^ 1] : pl->keys[pl->cur];
+  const uint32_t rb = row_bytes_for(pl, j);
+  launch_write_topk(pl->sel_slot, pl->sel_count, pl->sidx[0], pl->ctl, prev, base, pl->sb, j, rb, rows,
+                    pl->out_keys, pl->out_counts, s);
+  IG_CUDA(cudaGetLastError());
+  if (keys_out) IG_CUDA(cudaMemcpyAsync(keys_out, pl->out_keys, (size_t)rows * rb, cudaMemcpyDeviceToHost, s));
+  if (counts_out)
+    IG_CUDA(cudaMemcpyAsync(counts_out, pl->out_counts, (size_t)rows * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  IG_CUDA(cudaStreamSynchronize(s));
+  *k_out = rows;
+  return IG_OK;
+}
+
+ig_status intergrams_stats(ig_plan* pl, ig_pass_stats* out) {
+  if (!pl || !out) return fail(IG_EINVAL, "plan or out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  if (pl->last_j == 0) return fail(IG_ESTATE, "no pass has run yet");
+  IG_CUDA(cudaMemcpyAsync(pl->h_ctl, pl->ctl, sizeof(PassCtl), cudaMemcpyDeviceToHost, pl->stream));
+  IG_CUDA(cudaStreamSynchronize(pl->stream));
+  out->j = pl->last_j;
+  out->windows = windows_for(pl, pl->last_j);
+  out->survivors = pl->h_ctl->survivors;
+  out->registrations = pl->h_ctl->registrations;
+  out->nonzero_selected = pl->h_ctl->nsel;
+  out->scanned_bytes = pl->data_bytes;
+  return IG_OK;
+}
+
+void intergrams_free(ig_plan* pl) {
+  if (!pl) return;
+  cudaStreamSynchronize(pl->stream);
+  release(pl);
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal declarations shared by the sm_103a translation units of the
+// top-k n-gram library. Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "intergrams.h"
+
+namespace ig {
+
+constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
+constexpr int kHistBins = 4096;      // bins of one threshold-search level
+constexpr int kMaxLevels = 4;        // threshold-search levels (4096^k >= 2^32 at k = 3; one spare)
+constexpr int kSortDigits = 256;     // 8-bit digits of the final stable sort
+constexpr int kSortChunk = 1024;     // elements per one-warp block of the stable sort
+
+// Sticky device status bits (PassCtl::status).
+enum : uint32_t {
+  kStSetFull = 1u << 0,        // a per-sequence dedupe set filled up
+  kStTableFull = 1u << 1,      // the candidate probe table had no empty slot
+  kStCountOverflow = 1u << 2,  // a 32-bit count wrapped (Eq. 1 only)
+  kStQueue = 1u << 3,          // work queue inconsistency
+};
+
+// Device-side control block, one per plan. The pass fields are zeroed at the
+// start of each pass by a kernel, so a captured graph can replay a pass.
+struct PassCtl {
+  uint32_t queue;                    // next sequence to scan
+  uint32_t status;                   // sticky kStXxx bits (never cleared)
+  unsigned long long survivors;      // windows whose prefix was a candidate
+  unsigned long long registrations;  // count increments issued
+  // selection state
+  uint32_t target;                   // how many entries to keep (Z or k)
+  uint32_t max_count;
+  uint32_t nonzero;
+  uint32_t lo, hi;                   // threshold search range (inclusive)
+  uint32_t above;                    // entries with count > hi
+  uint32_t done;                     // threshold found
+  uint32_t thr;                      // selected: count > thr, plus the first need_eq with count == thr
+  uint32_t need_eq;
+  uint32_t nsel;                     // number selected
+  uint32_t take_all;                 // nonzero <= target: keep every nonzero entry
+  // Eq. 2 dedupe epochs: sequence s of the current pass uses epoch_base + s + 1
+  uint32_t epoch_base;
+  uint32_t epoch_next;
+  uint32_t gset_clear;               // epochs wrapped: clear the dedupe sets before the scan
+  uint32_t pad;
+};
+
+struct ScanArgs {
+  const uint8_t* data;
+  uint64_t data_bytes;
+  const uint64_t* offsets;
+  const uint32_t* order;       // sequences in scheduling order (longest first)
+  uint32_t m;
+  uint32_t j;                  // window length in symbols
+  uint64_t key_mask;           // low j*symbol_bits bits
+  const uint4* table;          // candidate probe table {key lo, key hi, id, 0}; null for the base pass
+  uint32_t table_log2;
+  uint32_t* counts;            // dense count table, indexed by slot
+  unsigned long long* gset;    // per-CTA global dedupe sets, (epoch << 32 | slot)
+  uint32_t gset_log2;          // log2 entries of each CTA's set
+  uint32_t count_mode;
+  uint32_t words_per_thread;   // 32-bit smem words of symbols per thread per tile
+  uint32_t sset_log2;          // log2 entries of the shared-memory dedupe set
+  uint32_t tile_words;         // 32-bit words in the shared-memory tile buffer
+  uint32_t check_overflow;     // Eq. 1 with >= 2^32 windows: detect count wrap
+  PassCtl* ctl;
+};
+
+// Launchers (ig_scan.cu)
+void launch_scan(const ScanArgs& a, uint32_t symbol_bits, bool base_pass, int grid, int threads,
+                 size_t smem, cudaStream_t s);
+int scan_max_ctas_per_sm(uint32_t symbol_bits, bool base_pass, int threads, size_t smem);
+cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem);
+
+// Launchers (ig_select.cu)
+void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint64_t gset_entries, cudaStream_t s);
+void launch_select(const uint32_t* counts, uint64_t ns, uint32_t target, PassCtl* ctl,
+                   uint32_t* hist /* kMaxLevels*kHistBins */, uint32_t* blk /* 2*G */, int G,
+                   uint32_t* sel_slot, uint32_t* sel_count, cudaStream_t s);
+void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap,
+                          uint32_t* idx_a, uint32_t* idx_b, uint32_t* key_a, uint32_t* key_b,
+                          uint32_t* hist /* kSortDigits * ceil(cap/kSortChunk) */, cudaStream_t s);
+
+// Launchers (ig_table.cu)
+void launch_build_candidates(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
+                             bool from_base, uint32_t symbol_bits, unsigned long long* keys_next,
+                             uint4* table, uint32_t table_log2, cudaStream_t s);
+void launch_write_topk(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
+                       const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
+                       uint32_t symbol_bits, uint32_t j, uint32_t row_bytes, uint32_t cap,
+                       uint8_t* keys_out, unsigned long long* counts_out, cudaStream_t s);
+
+// ------------------------------------------------------------- helpers
+
+__host__ __device__ inline uint32_t ceil_log2_u64(uint64_t x) {
+  uint32_t l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
+// Multiply-shift hashing (Dietzfelbinger, Hagerup, Katajainen, Penttonen,
+// "A reliable randomized algorithm for the closest-pair problem", 1997):
+// the top l bits of a*x mod 2^w for an odd multiplier a.
+__device__ __forceinline__ uint32_t hash64_top(uint64_t x, uint32_t l) {
+  return l == 0 ? 0u : (uint32_t)((x * 0x9E3779B97F4A7C15ull) >> (64 - l));
+}
+__device__ __forceinline__ uint32_t hash32_top(uint32_t x, uint32_t l) {
+  return l == 0 ? 0u : (x * 0x9E3779B1u) >> (32 - l);
+}
+
+}  // namespace ig

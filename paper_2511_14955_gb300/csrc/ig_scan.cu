@@ -1,0 +1,264 @@
+// Corpus scan of one pass (paper Algorithm 2 for the dense base pass,
+// Algorithm 3's inner loop for the candidate passes).
+//
+// A persistent grid pulls whole sequences from a queue ordered longest
+// first. A CTA owns its sequence: it streams it through shared memory in
+// tiles (each tile carries a halo of j-1 symbols so windows that cross a
+// tile edge are complete), every thread rolls a j-symbol key over a
+// contiguous run of windows, and
+//   base pass      : slot = the j-gram itself (sigma^j dense counters);
+//   candidate pass : the (j-1)-gram prefix is looked up in the probe table
+//                    of P^(j-1) (ids in lexicographic order); a hit is a
+//                    survivor with slot = id * sigma + last symbol.
+// Under Eq. 2 a survivor is counted only the first time its slot appears in
+// the sequence: the CTA keeps the sequence's slots in a shared-memory set and
+// spills to a CTA-private global set (entries stamped with a per-(pass,
+// sequence) epoch, so they never need clearing). This is the paper's
+// per-sequence bit vector C_i, stored sparsely. Under Eq. 1 every survivor
+// counts. Counting is an atomic increment of the dense slot counter
+// (the paper's C).
+#include "ig_internal.cuh"
+
+namespace ig {
+
+namespace {
+
+template <int SB>
+struct Sym {
+  static constexpr uint32_t kPerWord = 32 / SB;
+  static constexpr uint32_t kMask = (1u << SB) - 1u;
+};
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
+
+// Candidate lookup: id of `prefix` in P^(j-1), or kEmpty32.
+__device__ __forceinline__ uint32_t probe_table(const uint4* __restrict__ table, uint32_t log2,
+                                                uint64_t prefix, PassCtl* ctl) {
+  const uint32_t mask = (1u << log2) - 1u;
+  uint32_t h = hash64_top(prefix, log2);
+  const uint32_t lo = (uint32_t)prefix, hi = (uint32_t)(prefix >> 32);
+  for (uint32_t it = 0; it <= mask; ++it) {
+    uint4 e = __ldg(table + h);
+    if (e.z == kEmpty32) return kEmpty32;
+    if (e.x == lo && e.y == hi) return e.z;
+    h = (h + 1) & mask;
+  }
+  atomicOr(&ctl->status, kStTableFull);
+  return kEmpty32;
+}
+
+// Insert into the CTA-private global set; true if `slot` is new for this
+// (pass, sequence) epoch.
+__device__ __forceinline__ bool gset_insert(unsigned long long* set, uint32_t log2, uint32_t epoch,
+                                            uint32_t slot, PassCtl* ctl) {
+  const uint32_t mask = (1u << log2) - 1u;
+  uint32_t h = hash32_top(slot, log2);
+  const unsigned long long want = ((unsigned long long)epoch << 32) | slot;
+  uint32_t it = 0;
+  unsigned long long cur = *((volatile unsigned long long*)(set + h));
+  while (it <= mask) {
+    if ((uint32_t)(cur >> 32) == epoch) {
+      if ((uint32_t)cur == slot) return false;
+      h = (h + 1) & mask;
+      ++it;
+      cur = *((volatile unsigned long long*)(set + h));
+      continue;
+    }
+    unsigned long long old = atomicCAS(set + h, cur, want);
+    if (old == cur) return true;
+    cur = old;  // lost a race at this position: look at it again
+  }
+  atomicOr(&ctl->status, kStSetFull);
+  return false;
+}
+
+// Insert into the shared-memory set of the current sequence; falls back to
+// the global set when the bounded probe finds no room.
+__device__ __forceinline__ bool seq_first_seen(uint32_t* sset, uint32_t slog, unsigned long long* gset,
+                                               uint32_t glog, uint32_t epoch, uint32_t slot, PassCtl* ctl) {
+  const uint32_t mask = (1u << slog) - 1u;
+  uint32_t h = hash32_top(slot, slog);
+  const uint32_t maxp = mask < 31u ? mask + 1u : 32u;
+  for (uint32_t p = 0; p < maxp; ++p) {
+    uint32_t cur = sset[h];
+    if (cur == slot) return false;
+    if (cur == kEmpty32) {
+      uint32_t old = atomicCAS(sset + h, kEmpty32, slot);
+      if (old == kEmpty32) return true;
+      if (old == slot) return false;
+    }
+    h = (h + 1) & mask;
+  }
+  return gset_insert(gset, glog, epoch, slot, ctl);
+}
+
+template <int SB, bool BASE>
+__global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_item;
+  __shared__ unsigned long long s_surv, s_regs;
+
+  using S = Sym<SB>;
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+  const uint32_t R = a.words_per_thread * S::kPerWord;  // windows per thread per tile
+  const uint32_t tile_windows = R * nthr;
+  uint32_t* sset = smem;
+  uint32_t* tile = smem + (1u << a.sset_log2);
+  uint8_t* tile_b = reinterpret_cast<uint8_t*>(tile);
+  unsigned long long* gset = a.gset + ((unsigned long long)blockIdx.x << a.gset_log2);
+  const uint32_t j = a.j;
+  const uint32_t epoch_base = a.ctl->epoch_base;
+
+  unsigned long long my_surv = 0, my_regs = 0;
+  if (tid == 0) { s_surv = 0; s_regs = 0; }
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(&a.ctl->queue, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= a.m) break;
+    const uint32_t seq = a.order[item];
+    const uint64_t s0 = a.offsets[seq];
+    const uint64_t L = a.offsets[seq + 1] - s0;
+    if (L < j) continue;
+    const uint64_t W = L - j + 1;
+    const uint32_t epoch = epoch_base + seq + 1;
+    uint32_t slog = 0, glog = 0;
+    if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+      uint32_t need = ceil_log2_u64(2 * W);
+      slog = need < a.sset_log2 ? need : a.sset_log2;
+      if (slog < 1) slog = 1;
+      glog = need < a.gset_log2 ? need : a.gset_log2;
+      if (glog < 1) glog = 1;
+      for (uint32_t i = tid; i < (1u << slog); i += nthr) sset[i] = kEmpty32;
+    }
+
+    for (uint64_t w0 = 0; w0 < W; w0 += tile_windows) {
+      const uint32_t nwin = (uint32_t)((W - w0) < tile_windows ? (W - w0) : tile_windows);
+      const uint64_t gsym = s0 + w0;                     // first symbol of the tile
+      const uint64_t nsym = (uint64_t)nwin + j - 1;      // symbols the tile needs
+      const uint64_t b_first = (gsym * SB) >> 3;
+      const uint64_t b_end = ((gsym + nsym) * SB + 7) >> 3;
+      const uintptr_t addr_first = reinterpret_cast<uintptr_t>(a.data) + b_first;
+      const uintptr_t al = addr_first & ~(uintptr_t)15;
+      const uint32_t sym_off = (uint32_t)(addr_first - al) * S::kPerWord / 4u +
+                               (uint32_t)(gsym % (8u / SB));
+      const uint32_t nbytes = (uint32_t)((reinterpret_cast<uintptr_t>(a.data) + b_end - al + 15) & ~(uintptr_t)15);
+      const uintptr_t lo_ok = reinterpret_cast<uintptr_t>(a.data);
+      const uintptr_t hi_ok = lo_ok + a.data_bytes;
+      // stage the tile (+ halo) in shared memory; 16-byte vector loads where
+      // the whole vector lies inside the corpus, byte loads at the edges
+      for (uint32_t x = tid * 16u; x < nbytes; x += nthr * 16u) {
+        const uintptr_t p = al + x;
+        uint4 v;
+        if (p >= lo_ok && p + 16 <= hi_ok) {
+          v = __ldcs(reinterpret_cast<const uint4*>(p));
+        } else {
+          uint32_t w[4] = {0, 0, 0, 0};
+          for (int b = 0; b < 16; ++b) {
+            uintptr_t q = p + b;
+            uint32_t byte = (q >= lo_ok && q < hi_ok) ? *reinterpret_cast<const uint8_t*>(q) : 0u;
+            w[b >> 2] |= byte << (8 * (b & 3));
+          }
+          v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        *reinterpret_cast<uint4*>(tile_b + x) = v;
+      }
+      __syncthreads();
+
+      const uint32_t wb = tid * R;
+      if (wb < nwin) {
+        const uint32_t we = (wb + R) < nwin ? (wb + R) : nwin;
+        uint32_t s = sym_off + wb;
+        uint32_t widx = s / S::kPerWord, q = s % S::kPerWord;
+        uint32_t word = bswap32(tile[widx]);
+        uint64_t key = 0;
+        const uint32_t total = (we - wb) + j - 1;
+        for (uint32_t i = 0; i < total; ++i) {
+          const uint32_t sym = (word >> (32 - SB * (q + 1))) & S::kMask;
+          if (++q == S::kPerWord) {
+            q = 0;
+            ++widx;
+            word = (widx < a.tile_words) ? bswap32(tile[widx]) : 0u;
+          }
+          key = ((key << SB) | sym) & a.key_mask;
+          if (i + 1 < j) continue;
+          uint32_t slot;
+          if (BASE) {
+            slot = (uint32_t)key;
+          } else {
+            const uint32_t id = probe_table(a.table, a.table_log2, key >> SB, a.ctl);
+            if (id == kEmpty32) continue;
+            slot = (id << SB) | (uint32_t)(key & S::kMask);
+          }
+          ++my_surv;
+          bool count_it = true;
+          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE)
+            count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
+          if (count_it) {
+            ++my_regs;
+            if (a.check_overflow) {
+              if (atomicAdd(a.counts + slot, 1u) == 0xFFFFFFFFu) atomicOr(&a.ctl->status, kStCountOverflow);
+            } else {
+              atomicAdd(a.counts + slot, 1u);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // per-CTA statistics
+  for (int o = 16; o > 0; o >>= 1) {
+    my_surv += __shfl_down_sync(0xffffffffu, my_surv, o);
+    my_regs += __shfl_down_sync(0xffffffffu, my_regs, o);
+  }
+  if ((tid & 31) == 0) {
+    atomicAdd(&s_surv, my_surv);
+    atomicAdd(&s_regs, my_regs);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&a.ctl->survivors, s_surv);
+    atomicAdd(&a.ctl->registrations, s_regs);
+  }
+}
+
+template <int SB, bool BASE>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(scan_kernel<SB, BASE>);
+}
+
+void* pick(uint32_t symbol_bits, bool base_pass) {
+  if (symbol_bits == 8) return base_pass ? kernel_ptr<8, true>() : kernel_ptr<8, false>();
+  return base_pass ? kernel_ptr<2, true>() : kernel_ptr<2, false>();
+}
+
+}  // namespace
+
+cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem) {
+  return cudaFuncSetAttribute(pick(symbol_bits, base_pass), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+int scan_max_ctas_per_sm(uint32_t symbol_bits, bool base_pass, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(symbol_bits, base_pass), threads, smem) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+void launch_scan(const ScanArgs& a, uint32_t symbol_bits, bool base_pass, int grid, int threads,
+                 size_t smem, cudaStream_t s) {
+  if (symbol_bits == 8) {
+    if (base_pass) scan_kernel<8, true><<<grid, threads, smem, s>>>(a);
+    else scan_kernel<8, false><<<grid, threads, smem, s>>>(a);
+  } else {
+    if (base_pass) scan_kernel<2, true><<<grid, threads, smem, s>>>(a);
+    else scan_kernel<2, false><<<grid, threads, smem, s>>>(a);
+  }
+}
+
+}  // namespace ig

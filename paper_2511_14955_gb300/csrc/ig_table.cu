@@ -1,0 +1,89 @@
+// Candidate set P^(j) and result rows.
+//
+// After the selection of pass j the chosen slots are in slot order, which is
+// the byte order of the j-grams; their rank r becomes the id of the j-gram in
+// P^(j). Its key is rebuilt from the parent (j-1)-gram key and the last
+// symbol: key_j = key_{j-1}[slot / sigma] * sigma + slot % sigma (for the
+// dense base pass the slot is the j-gram itself). Keys are right-aligned
+// integers of j * symbol_bits <= 64 bits, so integer order is byte order.
+//
+// The probe table maps a key to its id: open addressing with linear probing
+// over 16-byte entries {key low, key high, id, 0}, multiply-shift hashed,
+// kept at or below the configured load so that lookups (one per window in the
+// next scan) touch about one 32-byte sector.
+#include "ig_internal.cuh"
+
+namespace ig {
+
+namespace {
+
+__global__ void table_clear_kernel(uint4* table, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    table[i] = make_uint4(0u, 0u, kEmpty32, 0u);
+}
+
+__device__ __forceinline__ unsigned long long key_of_slot(uint32_t slot, const unsigned long long* keys_prev,
+                                                          bool from_base, uint32_t sb) {
+  if (from_base) return slot;
+  return (keys_prev[slot >> sb] << sb) | (slot & ((1u << sb) - 1u));
+}
+
+__global__ void build_kernel(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
+                             bool from_base, uint32_t sb, unsigned long long* keys_next, uint4* table,
+                             uint32_t log2, PassCtl* ctl_w) {
+  const uint32_t n = ctl->nsel, mask = (1u << log2) - 1u;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const unsigned long long key = key_of_slot(sel_slot[r], keys_prev, from_base, sb);
+    keys_next[r] = key;
+    uint32_t h = hash64_top(key, log2);
+    bool placed = false;
+    for (uint32_t it = 0; it <= mask; ++it) {
+      uint32_t* idp = &table[h].z;
+      if (atomicCAS(idp, kEmpty32, r) == kEmpty32) {
+        table[h].x = (uint32_t)key;
+        table[h].y = (uint32_t)(key >> 32);
+        placed = true;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+    if (!placed) atomicOr(&ctl_w->status, kStTableFull);
+  }
+}
+
+__global__ void write_topk_kernel(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
+                                  const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
+                                  uint32_t sb, uint32_t j, uint32_t row_bytes, uint32_t cap, uint8_t* keys_out,
+                                  unsigned long long* counts_out) {
+  const uint32_t n = min(ctl->nsel, cap);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const uint32_t e = order[r];
+    const uint32_t slot = sel_slot[e];
+    counts_out[r] = sel_count[e];
+    const unsigned long long key = key_of_slot(slot, keys_prev, from_base, sb);
+    const uint32_t bits = j * sb;
+    const unsigned long long v = bits >= 64 ? key : key << (64 - bits);   // left-aligned
+    for (uint32_t b = 0; b < row_bytes; ++b) keys_out[(size_t)r * row_bytes + b] = (uint8_t)(v >> (56 - 8 * b));
+  }
+}
+
+}  // namespace
+
+void launch_build_candidates(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
+                             bool from_base, uint32_t symbol_bits, unsigned long long* keys_next, uint4* table,
+                             uint32_t table_log2, cudaStream_t s) {
+  const uint32_t n = 1u << table_log2;
+  table_clear_kernel<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, s>>>(table, n);
+  build_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, keys_prev, from_base, symbol_bits, keys_next, table,
+                                    table_log2, const_cast<PassCtl*>(ctl));
+}
+
+void launch_write_topk(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
+                       const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
+                       uint32_t symbol_bits, uint32_t j, uint32_t row_bytes, uint32_t cap, uint8_t* keys_out,
+                       unsigned long long* counts_out, cudaStream_t s) {
+  write_topk_kernel<<<256, 256, 0, s>>>(sel_slot, sel_count, order, ctl, keys_prev, from_base, symbol_bits, j,
+                                        row_bytes, cap, keys_out, counts_out);
+}
+
+}  // namespace ig

@@ -1,0 +1,175 @@
+"""GPU path vs the CPU oracle: bit-exact keys and counts (all integer work).
+
+Every test calls the CUDA library through its C ABI (paper_2511_14955_gb300
+.binding) and compares with oracle/ on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2511_14955_gb300 import binding as B  # noqa: E402
+from paper_2511_14955_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(data, off):
+    d = torch.from_numpy(np.array(data, copy=True)).cuda() if len(data) else torch.zeros(1, dtype=torch.uint8).cuda()
+    o = torch.from_numpy(np.ascontiguousarray(off).view(np.int64)).cuda()
+    return d, o
+
+
+def oracle_rows(keys, symbol_bits):
+    """Oracle symbol codes -> the library's packed row format."""
+    if symbol_bits == 8:
+        return keys
+    return np.stack([synth.pack_2bit(r) for r in keys]) if len(keys) else keys[:, : (keys.shape[1] + 3) // 4]
+
+
+def check_all_passes(data, off, *, n, k, Z, base_n, mode=0, symbol_bits=8, tuning=None, graph=False):
+    d, o = dev(data, off)
+    pl = B.Plan(d, o, n=n, k=k, candidates=Z, base_n=base_n, symbol_bits=symbol_bits, count_mode=mode,
+                tuning=tuning, graph=graph)
+    b = min(base_n, n)
+    seen = []
+    while True:
+        j = pl.step()
+        if j is None:
+            break
+        seen.append(j)
+        gk, gc, gj = pl.topk()
+        ek, ec = O.intergrams(data, off, n, k, Z, base_n=base_n, count_mode=mode, symbol_bits=symbol_bits,
+                              stop_j=j)
+        ek = oracle_rows(ek, symbol_bits)
+        assert gj == j
+        assert gk.shape == ek.shape, (j, gk.shape, ek.shape)
+        assert np.array_equal(gc, ec), f"counts differ at pass {j}"
+        assert np.array_equal(gk, ek), f"keys differ at pass {j}"
+        if mode == O.EQ1_EVERY_OCCURRENCE:
+            _, _, surv = O.intergrams(data, off, n, 1, Z, base_n=base_n, count_mode=mode,
+                                      symbol_bits=symbol_bits, stop_j=j, want_survivors=True)
+            assert pl.stats()["survivors"] == surv
+    assert seen == list(range(b, n + 1))
+    pl.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_markov_2mb_every_pass(mode):
+    """The 2 MiB Markov workload: n = 4, Z = 4096, k = 1024, base 1; top-k after every pass."""
+    data, off, _ = synth.make_corpus("markov_2mb")
+    check_all_passes(data, off, n=4, k=1024, Z=4096, base_n=1, mode=mode)
+
+
+@pytest.mark.parametrize("base_n", [1, 3])
+def test_malware_like_reduced(base_n):
+    """Malware-like byte law (motifs + zero blocks), reduced to 60 sequences of <= 32 KiB, n = 8."""
+    data, off, _ = synth.make_corpus("malware_8gb", m=60, max_len=32 * 1024)
+    check_all_passes(data, off, n=8, k=512, Z=2048, base_n=base_n)
+
+
+def test_largen_background_reduced():
+    data, off, _ = synth.make_corpus("largen_6gb", m=60, max_len=40000)
+    check_all_passes(data, off, n=8, k=300, Z=1500, base_n=2)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_dna_reduced(mode):
+    """2-bit packed DNA at arbitrary base offsets; k-mers up to 32 bases."""
+    data, off, bits = synth.make_corpus("genomic_5gbp", m=5, max_len=30011)
+    check_all_passes(data, off, n=16, k=400, Z=1600, base_n=8, mode=mode, symbol_bits=2)
+    check_all_passes(data, off, n=32, k=50, Z=300, base_n=12, mode=mode, symbol_bits=2)
+
+
+@pytest.mark.parametrize("tuning", [
+    dict(threads=256, words_per_thread=1, smem_set_log2=8, ctas_per_sm=4),   # tiny tiles, heavy spill
+    dict(threads=1024, words_per_thread=13, smem_set_log2=15, ctas_per_sm=1),
+    dict(threads=512, words_per_thread=3, smem_set_log2=10, table_load_pct=50),
+])
+def test_results_do_not_depend_on_tuning(tuning):
+    data, off, _ = synth.make_corpus("markov_2mb", seed=2)
+    check_all_passes(data, off, n=5, k=700, Z=3000, base_n=2, tuning=tuning)
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(0)
+    cases = [
+        [],                                     # no sequences
+        [b""],                                  # one empty sequence
+        [b"ab", b"", b"c"],                     # all shorter than n
+        [b"\x00" * 5000],                       # one zero run: a single n-gram
+        [bytes(rng.integers(0, 2, 3000).astype(np.uint8)) for _ in range(7)],   # binary alphabet
+        [b"abcd" * 100, b"abcd" * 3, b"dcba"],  # ties
+    ]
+    for seqs in cases:
+        lens = [len(s) for s in seqs]
+        off = np.zeros(len(seqs) + 1, np.uint64)
+        off[1:] = np.cumsum(lens) if seqs else []
+        data = np.frombuffer(b"".join(seqs), np.uint8) if sum(lens) else np.zeros(0, np.uint8)
+        for mode in (0, 1):
+            check_all_passes(data, off, n=4, k=5, Z=7, base_n=1, mode=mode)
+            check_all_passes(data, off, n=3, k=3, Z=3, base_n=3, mode=mode)   # n == base_n
+
+
+def test_k_equals_candidates_and_single_candidate():
+    data, off, _ = synth.make_corpus("markov_2mb", m=8, seed=5)
+    check_all_passes(data, off, n=6, k=64, Z=64, base_n=1)
+    check_all_passes(data, off, n=6, k=1, Z=1, base_n=1)
+
+
+def test_host_input_graph_rewind_and_unaligned():
+    data, off, _ = synth.make_corpus("markov_2mb", m=20, seed=9)
+    ek, ec = O.intergrams(data, off, 6, 200, 900, base_n=2)
+    # host buffers: the library copies them itself
+    pl = B.Plan(data, off, n=6, k=200, candidates=900, base_n=2, host_input=True)
+    pl.run()
+    gk, gc, _ = pl.topk()
+    assert np.array_equal(gk, ek) and np.array_equal(gc, ec)
+    pl.close()
+    # CUDA graph: capture on the first run, replay after rewind
+    d, o = dev(data, off)
+    pl = B.Plan(d, o, n=6, k=200, candidates=900, base_n=2, graph=True)
+    for _ in range(3):
+        pl.run()
+        gk, gc, _ = pl.topk()
+        assert np.array_equal(gk, ek) and np.array_equal(gc, ec)
+        pl.rewind()
+    pl.close()
+    # data pointer not 16-byte aligned
+    big = torch.zeros(len(data) + 64, dtype=torch.uint8, device="cuda")
+    big[3:3 + len(data)] = torch.from_numpy(data).cuda()
+    pl = B.Plan(big[3:3 + len(data)], o, n=6, k=200, candidates=900, base_n=2)
+    pl.run()
+    gk, gc, _ = pl.topk()
+    assert np.array_equal(gk, ek) and np.array_equal(gc, ec)
+    pl.close()
+
+
+def test_repeated_runs_identical():
+    data, off, _ = synth.make_corpus("malware_8gb", m=40, max_len=64 * 1024, seed=3)
+    d, o = dev(data, off)
+    outs = []
+    for _ in range(3):
+        pl = B.Plan(d, o, n=7, k=800, candidates=3000, base_n=3)
+        pl.run()
+        outs.append(pl.topk())
+        pl.close()
+    for x in outs[1:]:
+        assert np.array_equal(x[0], outs[0][0]) and np.array_equal(x[1], outs[0][1])
+
+
+def test_invalid_arguments_rejected():
+    data, off, _ = synth.make_corpus("markov_2mb", m=4)
+    d, o = dev(data, off)
+    bad = [dict(n=0, k=1, candidates=1), dict(n=4, k=10, candidates=5), dict(n=4, k=1, candidates=1 << 24),
+           dict(n=4, k=1, candidates=4, base_n=4), dict(n=4, k=1, candidates=4, symbol_bits=4),
+           dict(n=4, k=1, candidates=4, count_mode=2)]
+    for kw in bad:
+        with pytest.raises(B.IntergramsError) as ei:
+            B.Plan(d, o, **kw)
+        assert ei.value.status == -1
+    bad_off = off.copy()
+    bad_off[2], bad_off[3] = bad_off[3], bad_off[2]
+    with pytest.raises(B.IntergramsError):
+        B.Plan(d, dev(data, bad_off)[1], n=4, k=1, candidates=4)
