@@ -54,6 +54,8 @@ typedef enum {
 #define IG_F_GRAPH      (1u << 1)  /* capture each pass's launch sequence as a CUDA
                                       graph on first use and replay it afterwards */
 #define IG_F_AUTOTUNE   (1u << 2)  /* let the autotuner pick the tuning knobs left at 0 */
+#define IG_F_TIMING     (1u << 3)  /* record CUDA events around every scan kernel and pass
+                                      (on the plan's stream) for intergrams_timings */
 
 typedef struct {
   uint32_t n;            /* target n-gram length in symbols: 1..64 (bytes), 1..32 (2-bit) */
@@ -119,8 +121,10 @@ ig_status intergrams_run(ig_plan* pl);
  * intergrams_rewind - return the plan to its state before the first pass so
  * the whole job can run again over the same corpus buffers (whose contents
  * may have changed, as long as the offsets did not). Tables are reused; with
- * IG_F_GRAPH a graph captured by intergrams_run is replayed. Stream-ordered,
- * no synchronisation.
+ * IG_F_GRAPH a graph captured by intergrams_run is replayed. With
+ * IG_F_HOST_INPUT the host data buffer given to intergrams_plan (which must
+ * still be valid) is copied to the device again, so the rerun sees its
+ * current contents. Stream-ordered, no synchronisation.
  */
 ig_status intergrams_rewind(ig_plan* pl);
 
@@ -152,6 +156,19 @@ typedef struct {
 } ig_pass_stats;
 
 ig_status intergrams_stats(ig_plan* pl, ig_pass_stats* out);
+
+/*
+ * intergrams_timings - device times of the latest run, from CUDA events
+ * recorded on the plan's stream (requires IG_F_TIMING; synchronises).
+ *   scan_ms / pass_ms : arrays of `cap` floats, or NULL: per pass, the scan
+ *                       kernel's duration and the whole pass's duration
+ *                       (reset, scan, selection, candidate build), in pass order.
+ *   npasses           : receives the number of passes of the latest run.
+ *   kernels           : optional; receives the number of kernels the latest
+ *                       run launched (graph replays count their kernel nodes).
+ */
+ig_status intergrams_timings(ig_plan* pl, float* scan_ms, float* pass_ms, uint32_t cap,
+                             uint32_t* npasses, uint32_t* kernels);
 
 /* Release every resource of the plan (stream-ordered frees). NULL is ignored. */
 void intergrams_free(ig_plan* pl);

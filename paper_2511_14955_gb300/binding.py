@@ -22,10 +22,11 @@ COUNT_EVERY_OCCURRENCE = 1
 F_HOST_INPUT = 1 << 0
 F_GRAPH = 1 << 1
 F_AUTOTUNE = 1 << 2
+F_TIMING = 1 << 3
 
 # every symbol include/intergrams.h declares
 EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_rewind", "intergrams_topk",
-           "intergrams_stats", "intergrams_free", "intergrams_last_error"]
+           "intergrams_stats", "intergrams_timings", "intergrams_free", "intergrams_last_error"]
 
 
 class IgParams(ctypes.Structure):
@@ -82,6 +83,8 @@ def load(build_if_missing: bool = True):
     lib.intergrams_topk.argtypes = [P, P, P, U32, ctypes.POINTER(U32), ctypes.POINTER(U32)]
     lib.intergrams_stats.restype = ctypes.c_int
     lib.intergrams_stats.argtypes = [P, ctypes.POINTER(IgPassStats)]
+    lib.intergrams_timings.restype = ctypes.c_int
+    lib.intergrams_timings.argtypes = [P, P, P, U32, ctypes.POINTER(U32), ctypes.POINTER(U32)]
     lib.intergrams_free.restype = None
     lib.intergrams_free.argtypes = [P]
     lib.intergrams_last_error.restype = ctypes.c_char_p
@@ -115,10 +118,10 @@ class Plan:
 
     def __init__(self, data, offsets, *, n: int, k: int, candidates: int, base_n: int = 3,
                  symbol_bits: int = 8, count_mode: int = COUNT_ONCE_PER_SEQUENCE, graph: bool = False,
-                 host_input: bool = False, stream=None, tuning: dict | None = None):
+                 host_input: bool = False, timing: bool = False, stream=None, tuning: dict | None = None):
         self._lib = load()
         self._h = ctypes.c_void_p(None)
-        flags = (F_GRAPH if graph else 0) | (F_HOST_INPUT if host_input else 0)
+        flags = (F_GRAPH if graph else 0) | (F_HOST_INPUT if host_input else 0) | (F_TIMING if timing else 0)
         self.params = IgParams(n, k, candidates, base_n, symbol_bits, count_mode, flags)
         tun = IgTuning(**(tuning or {}))
         if host_input:
@@ -174,6 +177,19 @@ class Plan:
         s = IgPassStats()
         _check(self._lib, self._lib.intergrams_stats(self._h, ctypes.byref(s)), "intergrams_stats")
         return {f: getattr(s, f) for f, _ in IgPassStats._fields_}
+
+    def timings(self):
+        """Per-pass scan-kernel and pass durations (ms) of the latest run, and
+        the number of kernels launched since the last rewind."""
+        cap = 128
+        scan = np.zeros(cap, np.float32)
+        pas = np.zeros(cap, np.float32)
+        npass, kern = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        _check(self._lib, self._lib.intergrams_timings(self._h, scan.ctypes.data, pas.ctypes.data, cap,
+                                                       ctypes.byref(npass), ctypes.byref(kern)),
+               "intergrams_timings")
+        r = npass.value
+        return scan[:r].copy(), pas[:r].copy(), kern.value
 
     def close(self):
         if self._h and self._h.value:

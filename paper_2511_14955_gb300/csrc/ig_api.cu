@@ -94,6 +94,11 @@ struct ig_plan {
   unsigned long long* out_counts = nullptr;
   uint32_t out_cap = 0;
 
+  const void* host_data = nullptr;   // IG_F_HOST_INPUT: re-read by intergrams_rewind
+  // IG_F_TIMING: events around each pass and its scan, indexed by j - b
+  std::vector<cudaEvent_t> ev_pass0, ev_pass1, ev_scan0, ev_scan1;
+  uint32_t kernels = 0;              // kernels launched since the last rewind
+  uint32_t graph_kernels = 0;        // kernels in the captured graph
   cudaGraphExec_t graph = nullptr;  // full job from the first pass (IG_F_GRAPH)
   cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
   bool check_overflow = false;
@@ -115,6 +120,9 @@ uint64_t windows_for(const ig_plan* pl, uint32_t j) {
 void release(ig_plan* pl) {
   if (!pl) return;
   if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  for (auto* v : {&pl->ev_pass0, &pl->ev_pass1, &pl->ev_scan0, &pl->ev_scan1})
+    for (cudaEvent_t e : *v)
+      if (e) cudaEventDestroy(e);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   void* ptrs[] = {pl->own_data, pl->own_offsets, pl->counts, pl->table, pl->keys[0], pl->keys[1],
                   pl->sel_slot, pl->sel_count, pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
@@ -126,11 +134,17 @@ void release(ig_plan* pl) {
 }
 
 // Enqueue pass j (no host synchronisation).
-void enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
+// Enqueue pass j (no host synchronisation); returns the kernels launched.
+uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   const bool base = (j == pl->b);
+  const bool timing = (pl->p.flags & IG_F_TIMING) != 0;
+  const uint32_t ti = j - pl->b;
   const uint64_t ns = base ? pl->nslots_base : pl->nslots_cand;
-  launch_pass_reset(pl->ctl, pl->m, pl->p.count_mode == IG_COUNT_ONCE_PER_SEQUENCE ? pl->gset : nullptr,
-                    pl->gset_entries, s);
+  uint32_t kernels = 0;
+  if (timing) cudaEventRecordWithFlags(pl->ev_pass0[ti], s, cudaEventRecordExternal);
+  const bool seq_mode = pl->p.count_mode == IG_COUNT_ONCE_PER_SEQUENCE;
+  launch_pass_reset(pl->ctl, pl->m, seq_mode ? pl->gset : nullptr, pl->gset_entries, s);
+  kernels += seq_mode ? 3 : 1;
   cudaMemsetAsync(pl->counts, 0, ns * sizeof(uint32_t), s);
   ScanArgs a{};
   a.data = pl->data;
@@ -151,14 +165,23 @@ void enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.tile_words = pl->tile_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
   a.ctl = pl->ctl;
-  if (pl->m > 0) launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
+  if (timing) cudaEventRecordWithFlags(pl->ev_scan0[ti], s, cudaEventRecordExternal);
+  if (pl->m > 0) {
+    launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
+    kernels += 1;
+  }
+  if (timing) cudaEventRecordWithFlags(pl->ev_scan1[ti], s, cudaEventRecordExternal);
   const uint32_t target = (j < pl->p.n) ? pl->p.candidates : pl->p.k;
   launch_select(pl->counts, ns, target, pl->ctl, pl->hist, pl->blk, pl->G, pl->sel_slot, pl->sel_count, s);
+  kernels += 12;
   if (j < pl->p.n) {
     const int nxt = pl->cur ^ 1;
     launch_build_candidates(pl->sel_slot, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], pl->table,
                             pl->table_log2, s);
+    kernels += 2;
   }
+  if (timing) cudaEventRecordWithFlags(pl->ev_pass1[ti], s, cudaEventRecordExternal);
+  return kernels;
 }
 
 // After pass j has been enqueued: bookkeeping on the host.
@@ -255,6 +278,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
                               cudaMemcpyHostToDevice, pl->stream));
     pl->data = pl->own_data;
     pl->offsets = pl->own_offsets;
+    pl->host_data = data;
   } else {
     pl->data = reinterpret_cast<const uint8_t*>(data);
     pl->offsets = offsets;
@@ -330,6 +354,13 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   PLAN_CUDA(dev_alloc(&pl->ctl, 1));
   PLAN_CUDA(cudaMemsetAsync(pl->ctl, 0, sizeof(PassCtl), pl->stream));
   PLAN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&pl->h_ctl), sizeof(PassCtl)));
+  if (p->flags & IG_F_TIMING) {
+    const uint32_t np = p->n - pl->b + 1;
+    for (auto* v : {&pl->ev_pass0, &pl->ev_pass1, &pl->ev_scan0, &pl->ev_scan1}) {
+      v->assign(np, nullptr);
+      for (auto& e : *v) PLAN_CUDA(cudaEventCreate(&e));
+    }
+  }
   pl->out_cap = p->k;
   PLAN_CUDA(dev_alloc(&pl->out_keys, (size_t)pl->out_cap * row_bytes_for(pl, p->n) + 8));
   PLAN_CUDA(dev_alloc(&pl->out_counts, pl->out_cap));
@@ -353,7 +384,7 @@ ig_status intergrams_pass(ig_plan* pl, uint32_t* j_done) {
   if (!pl) return fail(IG_EINVAL, "plan is NULL");
   if (pl->next_j > pl->p.n) return IG_DONE;
   const uint32_t j = pl->next_j;
-  enqueue_pass(pl, j, pl->stream);
+  pl->kernels += enqueue_pass(pl, j, pl->stream);
   IG_CUDA(cudaGetLastError());
   finish_pass_host(pl, j);
   if (j_done) *j_done = j;
@@ -373,8 +404,9 @@ ig_status intergrams_run(ig_plan* pl) {
       if (!pl->cap_stream) IG_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
       IG_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
       const int cur0 = pl->cur;
+      pl->graph_kernels = 0;
       for (uint32_t j = pl->b; j <= pl->p.n; ++j) {
-        enqueue_pass(pl, j, pl->cap_stream);
+        pl->graph_kernels += enqueue_pass(pl, j, pl->cap_stream);
         if (j < pl->p.n) pl->cur ^= 1;
       }
       pl->cur = cur0;
@@ -385,11 +417,12 @@ ig_status intergrams_run(ig_plan* pl) {
       if (e != cudaSuccess) return fail(IG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     IG_CUDA(cudaGraphLaunch(pl->graph, pl->stream));
+    pl->kernels += pl->graph_kernels;
     for (uint32_t j = pl->b; j <= pl->p.n; ++j) finish_pass_host(pl, j);
     return read_status(pl);
   }
   for (uint32_t j = pl->next_j; j <= pl->p.n; ++j) {
-    enqueue_pass(pl, j, pl->stream);
+    pl->kernels += enqueue_pass(pl, j, pl->stream);
     finish_pass_host(pl, j);
   }
   IG_CUDA(cudaGetLastError());
@@ -403,6 +436,9 @@ ig_status intergrams_rewind(ig_plan* pl) {
   pl->next_j = pl->b;
   pl->last_j = 0;
   pl->nsel_last = 0;
+  pl->kernels = 0;
+  if ((pl->p.flags & IG_F_HOST_INPUT) && pl->data_bytes)
+    IG_CUDA(cudaMemcpyAsync(pl->own_data, pl->host_data, pl->data_bytes, cudaMemcpyHostToDevice, pl->stream));
   return IG_OK;
 }
 
@@ -426,6 +462,7 @@ ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out, 
   const uint32_t rb = row_bytes_for(pl, j);
   launch_write_topk(pl->sel_slot, pl->sel_count, pl->sidx[0], pl->ctl, prev, base, pl->sb, j, rb, rows,
                     pl->out_keys, pl->out_counts, s);
+  pl->kernels += 14;  // sort: init + 4 x (histogram, scan, scatter); write
   IG_CUDA(cudaGetLastError());
   if (keys_out) IG_CUDA(cudaMemcpyAsync(keys_out, pl->out_keys, (size_t)rows * rb, cudaMemcpyDeviceToHost, s));
   if (counts_out)
@@ -447,6 +484,24 @@ ig_status intergrams_stats(ig_plan* pl, ig_pass_stats* out) {
   out->registrations = pl->h_ctl->registrations;
   out->nonzero_selected = pl->h_ctl->nsel;
   out->scanned_bytes = pl->data_bytes;
+  return IG_OK;
+}
+
+ig_status intergrams_timings(ig_plan* pl, float* scan_ms, float* pass_ms, uint32_t cap, uint32_t* npasses,
+                             uint32_t* kernels) {
+  g_last_error.clear();
+  if (!pl || !npasses) return fail(IG_EINVAL, "plan or npasses is NULL");
+  *npasses = 0;
+  if (kernels) *kernels = pl->kernels;
+  if (!(pl->p.flags & IG_F_TIMING)) return fail(IG_ESTATE, "plan was made without IG_F_TIMING");
+  if (pl->last_j == 0) return IG_OK;
+  IG_CUDA(cudaStreamSynchronize(pl->stream));
+  const uint32_t np = pl->last_j - pl->b + 1;
+  for (uint32_t i = 0; i < np && i < cap; ++i) {
+    if (scan_ms) IG_CUDA(cudaEventElapsedTime(scan_ms + i, pl->ev_scan0[i], pl->ev_scan1[i]));
+    if (pass_ms) IG_CUDA(cudaEventElapsedTime(pass_ms + i, pl->ev_pass0[i], pl->ev_pass1[i]));
+  }
+  *npasses = np;
   return IG_OK;
 }
 
