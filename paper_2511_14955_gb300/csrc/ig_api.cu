@@ -141,7 +141,11 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   const uint32_t ti = j - pl->b;
   const uint64_t ns = base ? pl->nslots_base : pl->nslots_cand;
   uint32_t kernels = 0;
-  if (timing) cudaEventRecordWithFlags(pl->ev_pass0[ti], s, cudaEventRecordExternal);
+  // inside a stream capture an event record must be an explicit graph node
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (timing) cudaStreamIsCapturing(s, &cs);
+  const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (timing) cudaEventRecordWithFlags(pl->ev_pass0[ti], s, evf);
   const bool seq_mode = pl->p.count_mode == IG_COUNT_ONCE_PER_SEQUENCE;
   launch_pass_reset(pl->ctl, pl->m, seq_mode ? pl->gset : nullptr, pl->gset_entries, s);
   kernels += seq_mode ? 3 : 1;
@@ -165,12 +169,12 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.tile_words = pl->tile_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
   a.ctl = pl->ctl;
-  if (timing) cudaEventRecordWithFlags(pl->ev_scan0[ti], s, cudaEventRecordExternal);
+  if (timing) cudaEventRecordWithFlags(pl->ev_scan0[ti], s, evf);
   if (pl->m > 0) {
     launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
     kernels += 1;
   }
-  if (timing) cudaEventRecordWithFlags(pl->ev_scan1[ti], s, cudaEventRecordExternal);
+  if (timing) cudaEventRecordWithFlags(pl->ev_scan1[ti], s, evf);
   const uint32_t target = (j < pl->p.n) ? pl->p.candidates : pl->p.k;
   launch_select(pl->counts, ns, target, pl->ctl, pl->hist, pl->blk, pl->G, pl->sel_slot, pl->sel_count, s);
   kernels += 12;
@@ -180,7 +184,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
                             pl->table_log2, s);
     kernels += 2;
   }
-  if (timing) cudaEventRecordWithFlags(pl->ev_pass1[ti], s, cudaEventRecordExternal);
+  if (timing) cudaEventRecordWithFlags(pl->ev_pass1[ti], s, evf);
   return kernels;
 }
 

@@ -146,6 +146,23 @@ def test_host_input_graph_rewind_and_unaligned():
     pl.close()
 
 
+def test_timing_events_in_both_launch_modes():
+    data, off, _ = synth.make_corpus("markov_2mb", m=12, seed=4)
+    d, o = dev(data, off)
+    for graph in (False, True):
+        pl = B.Plan(d, o, n=5, k=100, candidates=400, base_n=2, graph=graph, timing=True)
+        for _ in range(2):
+            pl.rewind()
+            if graph:
+                pl.run()
+            else:
+                while pl.step() is not None:
+                    pass
+            scan, pas, kern = pl.timings()
+            assert len(scan) == 4 and (scan > 0).all() and (pas >= scan).all() and kern > 0
+        pl.close()
+
+
 def test_repeated_runs_identical():
     data, off, _ = synth.make_corpus("malware_8gb", m=40, max_len=64 * 1024, seed=3)
     d, o = dev(data, off)
