@@ -170,6 +170,42 @@ ig_status intergrams_stats(ig_plan* pl, ig_pass_stats* out);
 ig_status intergrams_timings(ig_plan* pl, float* scan_ms, float* pass_ms, uint32_t cap,
                              uint32_t* npasses, uint32_t* kernels);
 
+/*
+ * intergrams_dense_topk_static - exact top-k n-grams of a short length n,
+ * computed WITHOUT allocating anything (no counterpart in the paper).
+ *
+ * For callers that must not allocate device memory when they ask for an
+ * answer: code inside a memory pool that owns the device budget, hot paths
+ * with a no-allocation contract (allocation can synchronise the device or
+ * fail under fragmentation), embedders that forbid cudaMalloc after start-up.
+ * It runs the planned path's dense counting pass, selection and ordering
+ * kernels with every table placed in one file-scope device array of 40 MiB
+ * that the library holds on each GPU that loads it, until the process exits.
+ *
+ *   p            : n, k, symbol_bits and count_mode are used (candidates,
+ *                  base_n and flags are ignored). Limits of the fixed scratch:
+ *                  sigma^n <= 65536 (n <= 2 bytes or n <= 8 bases), k <= 65536,
+ *                  m <= 2^20 sequences; anything larger returns IG_EINVAL.
+ *   data, offsets: DEVICE inputs, as for intergrams_plan (offsets has m + 1
+ *                  entries; total_symbols = offsets[m], given by the caller).
+ *   stream       : cudaStream_t the work is ordered on (not synchronised).
+ *   keys_out     : DEVICE buffer of k * ceil(n * symbol_bits / 8) bytes.
+ *   counts_out   : DEVICE buffer of k uint64 counts.
+ *   rows_out     : DEVICE uint32: number of rows written (min(k, #nonzero)).
+ * Rows are in the same order and format as intergrams_topk after a run with
+ * n = base_n. Calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture. Every call reuses the same array, which keeps
+ * the previous call's contents (the call clears what must start at zero), so
+ * calls whose work overlaps on the GPU - from two streams or two threads -
+ * race and give wrong results: serialise them.
+ */
+ig_status intergrams_dense_topk_static(const ig_params* p, const void* data, const uint64_t* offsets,
+                                       uint32_t m, uint64_t total_symbols, void* stream,
+                                       uint8_t* keys_out, uint64_t* counts_out, uint32_t* rows_out);
+
 /* Release every resource of the plan (stream-ordered frees). NULL is ignored. */
 void intergrams_free(ig_plan* pl);
 

@@ -26,7 +26,8 @@ F_TIMING = 1 << 3
 
 # every symbol include/intergrams.h declares
 EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_rewind", "intergrams_topk",
-           "intergrams_stats", "intergrams_timings", "intergrams_free", "intergrams_last_error"]
+           "intergrams_stats", "intergrams_timings", "intergrams_free", "intergrams_last_error",
+           "intergrams_dense_topk_static"]
 
 
 class IgParams(ctypes.Structure):
@@ -87,6 +88,8 @@ def load(build_if_missing: bool = True):
     lib.intergrams_timings.argtypes = [P, P, P, U32, ctypes.POINTER(U32), ctypes.POINTER(U32)]
     lib.intergrams_free.restype = None
     lib.intergrams_free.argtypes = [P]
+    lib.intergrams_dense_topk_static.restype = ctypes.c_int
+    lib.intergrams_dense_topk_static.argtypes = [ctypes.POINTER(IgParams), P, P, U32, ctypes.c_uint64, P, P, P, P]
     lib.intergrams_last_error.restype = ctypes.c_char_p
     lib.intergrams_last_error.argtypes = []
     _lib = lib
@@ -207,3 +210,26 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def dense_topk_static(data, offsets, *, n: int, k: int, symbol_bits: int = 8,
+                      count_mode: int = COUNT_ONCE_PER_SEQUENCE, total_symbols: int, stream=None,
+                      keys_out=None, counts_out=None, rows_out=None):
+    """Allocation-free exact top-k of short n-grams (intergrams_dense_topk_static).
+
+    ``data``/``offsets`` are CUDA tensors; ``keys_out`` (uint8, k * row bytes),
+    ``counts_out`` (int64, k) and ``rows_out`` (int32, 1) are caller-owned CUDA
+    tensors. The library allocates nothing; the work is enqueued on ``stream``
+    (default: torch's current stream) and not synchronised.
+    """
+    lib = load()
+    m = len(offsets) - 1
+    params = IgParams(n, k, k, n, symbol_bits, count_mode, 0)
+    if stream is None:
+        import torch
+        stream_ptr = torch.cuda.current_stream().cuda_stream
+    else:
+        stream_ptr = getattr(stream, "cuda_stream", stream)
+    st = lib.intergrams_dense_topk_static(ctypes.byref(params), _ptr(data), _ptr(offsets), m, int(total_symbols),
+                                          stream_ptr, _ptr(keys_out), _ptr(counts_out), _ptr(rows_out))
+    _check(lib, st, "intergrams_dense_topk_static")

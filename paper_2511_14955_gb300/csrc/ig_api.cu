@@ -44,6 +44,11 @@ cudaError_t dev_alloc(T** p, size_t count) {
 
 }  // namespace
 
+namespace ig {
+// Lets other translation units record a message for intergrams_last_error().
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ig
+
 struct ig_plan {
   ig_params p{};
   ig_tuning t{};

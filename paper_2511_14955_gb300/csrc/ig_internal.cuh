@@ -77,6 +77,8 @@ void launch_scan(const ScanArgs& a, uint32_t symbol_bits, bool base_pass, int gr
                  size_t smem, cudaStream_t s);
 int scan_max_ctas_per_sm(uint32_t symbol_bits, bool base_pass, int threads, size_t smem);
 cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem);
+// Raise (never lower) the scan kernel's dynamic shared-memory limit to `smem`.
+cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem);
 
 // Launchers (ig_select.cu)
 void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint64_t gset_entries, cudaStream_t s);

@@ -242,6 +242,14 @@ cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t sme
                               (int)smem);
 }
 
+cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, pick(symbol_bits, base_pass));
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return scan_set_smem_limit(symbol_bits, base_pass, smem);
+}
+
 int scan_max_ctas_per_sm(uint32_t symbol_bits, bool base_pass, int threads, size_t smem) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(symbol_bits, base_pass), threads, smem) !=
