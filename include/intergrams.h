@@ -77,7 +77,8 @@ typedef struct {
   uint32_t words_per_thread; /* 32-bit smem words of symbols each thread scans per tile (odd, 1..31) */
   uint32_t smem_set_log2;    /* log2 entries of the per-sequence shared-memory dedupe set (8..15) */
   uint32_t table_load_pct;   /* maximum load of the candidate probe table, percent (10..50) */
-  uint32_t hot_log2;         /* log2 entries of the shared-memory hot candidate cache (0 = off, 6..12) */
+  uint32_t hot_log2;         /* log2 entries of the shared-memory cache of the most frequent
+                                candidates in front of the probe table (6..13; default 11) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -84,9 +84,13 @@ struct ig_plan {
   int G = 1024;
   uint32_t *sidx[2] = {nullptr, nullptr}, *skey[2] = {nullptr, nullptr}, *shist = nullptr;
   uint32_t sort_cap = 0;
-  unsigned long long* gset = nullptr;
-  uint32_t gset_log2 = 1;
-  uint64_t gset_entries = 0;
+  uint32_t* alive[2] = {nullptr, nullptr};  // survivor bitmasks, ping-pong by pass parity
+  uint64_t alive_words = 0;
+  uint4* hot = nullptr;                      // hot cache of the latest candidate set
+  unsigned long long* hot_pick = nullptr;
+  uint32_t hot_log2 = 0;
+  uint32_t* spill = nullptr;         // Eq. 2: per scan CTA, spill list + partition buffer
+  uint64_t spill_cap = 0;
   PassCtl* ctl = nullptr;
   PassCtl* h_ctl = nullptr;  // pinned mirror for status reads
   uint32_t* d_order = nullptr;
@@ -131,7 +135,8 @@ void release(ig_plan* pl) {
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   void* ptrs[] = {pl->own_data, pl->own_offsets, pl->counts, pl->table, pl->keys[0], pl->keys[1],
                   pl->sel_slot, pl->sel_count, pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
-                  pl->skey[1], pl->shist, pl->gset, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts};
+                  pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
+                  pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
@@ -152,8 +157,8 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (timing) cudaEventRecordWithFlags(pl->ev_pass0[ti], s, evf);
   const bool seq_mode = pl->p.count_mode == IG_COUNT_ONCE_PER_SEQUENCE;
-  launch_pass_reset(pl->ctl, pl->m, seq_mode ? pl->gset : nullptr, pl->gset_entries, s);
-  kernels += seq_mode ? 3 : 1;
+  launch_pass_reset(pl->ctl, pl->m, nullptr, 0, s);
+  kernels += 1;
   cudaMemsetAsync(pl->counts, 0, ns * sizeof(uint32_t), s);
   ScanArgs a{};
   a.data = pl->data;
@@ -166,13 +171,23 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.table = base ? nullptr : pl->table;
   a.table_log2 = pl->table_log2;
   a.counts = pl->counts;
-  a.gset = pl->gset;
-  a.gset_log2 = pl->gset_log2;
+  a.gset = nullptr;
+  a.gset_log2 = 0;
+  a.spill = seq_mode ? pl->spill : nullptr;
+  a.spill_cap = pl->spill_cap;
+  a.spill_extra_log2 = 0;
   a.count_mode = pl->p.count_mode;
   a.words_per_thread = pl->t.words_per_thread;
   a.sset_log2 = pl->t.smem_set_log2;
   a.tile_words = pl->tile_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
+  // pass j reads the survivors of pass j-1 (written by candidate passes only)
+  // and writes its own when pass j+1 will read them
+  a.alive_in = (j >= pl->b + 2) ? pl->alive[(j - 1) & 1u] : nullptr;
+  a.alive_out = (j >= pl->b + 1 && j + 1 <= pl->p.n) ? pl->alive[j & 1u] : nullptr;
+  if (a.alive_out) cudaMemsetAsync(a.alive_out, 0, pl->alive_words * sizeof(uint32_t), s);
+  a.hot = pl->hot;
+  a.hot_log2 = base ? 0u : pl->hot_log2;
   a.ctl = pl->ctl;
   if (timing) cudaEventRecordWithFlags(pl->ev_scan0[ti], s, evf);
   if (pl->m > 0) {
@@ -188,6 +203,10 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
     launch_build_candidates(pl->sel_slot, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], pl->table,
                             pl->table_log2, s);
     kernels += 2;
+    if (pl->hot_log2) {
+      launch_build_hot(pl->keys[nxt], pl->sel_count, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
+      kernels += 3;
+    }
   }
   if (timing) cudaEventRecordWithFlags(pl->ev_pass1[ti], s, evf);
   return kernels;
@@ -296,14 +315,15 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   // tuning (defaults; the autotuner in the binding may override)
   ig_tuning t{};
   if (tuning) t = *tuning;
-  if (!t.ctas_per_sm) t.ctas_per_sm = 2;
-  if (!t.threads) t.threads = 512;
+  if (!t.ctas_per_sm) t.ctas_per_sm = 1;
+  if (!t.threads) t.threads = 1024;
   if (!t.words_per_thread) t.words_per_thread = 9;
-  if (!t.smem_set_log2) t.smem_set_log2 = 14;
+  if (!t.smem_set_log2) t.smem_set_log2 = 15;
   if (!t.table_load_pct) t.table_load_pct = 25;
+  if (!t.hot_log2) t.hot_log2 = 11;
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
-      t.table_load_pct < 10 || t.table_load_pct > 50)
+      t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13)
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;
 
@@ -327,25 +347,29 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   pl->tile_words = (uint32_t)((tile_syms * pl->sb + 31) / 32) + 8;
   pl->tile_words = (pl->tile_words + 3) & ~3u;
   pl->scan_threads = (int)t.threads;
-  pl->scan_smem = ((size_t)4 << t.smem_set_log2) + (size_t)pl->tile_words * 4;
+  pl->hot_log2 = (pl->b < p->n) ? t.hot_log2 : 0u;
+  pl->scan_smem = ((size_t)4 << t.smem_set_log2) + (size_t)12 * (pl->hot_log2 ? (1u << pl->hot_log2) : 0u) +
+                  (size_t)pl->tile_words * 4;
   for (bool base : {true, false}) PLAN_CUDA(scan_set_smem_limit(pl->sb, base, pl->scan_smem));
   int occ = std::min(scan_max_ctas_per_sm(pl->sb, false, pl->scan_threads, pl->scan_smem),
                      scan_max_ctas_per_sm(pl->sb, true, pl->scan_threads, pl->scan_smem));
   if (occ < 1) return bail(fail(IG_EINVAL, "scan kernel does not fit on an SM with these tuning knobs"));
   pl->scan_grid = pl->sms * (int)std::min<uint32_t>(t.ctas_per_sm, (uint32_t)occ);
 
-  // Eq. 2 dedupe sets: one per scan CTA, sized for the longest sequence
-  if (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-    pl->gset_log2 = ceil_log2_u64(2 * std::max<uint64_t>(pl->max_len, 1));
-    pl->gset_log2 = std::max<uint32_t>(pl->gset_log2, 5);
-    pl->gset_log2 = std::min<uint32_t>(pl->gset_log2, 24);
-    pl->gset_entries = (uint64_t)pl->scan_grid << pl->gset_log2;
-  } else {
-    pl->gset_log2 = 1;
-    pl->gset_entries = 2;
-  }
+  // Eq. 2 spill buffers: per scan CTA a list and a partition buffer, each
+  // holding every window of the longest sequence
+  if (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE) pl->spill_cap = std::max<uint64_t>(pl->max_len, 1);
 
   PLAN_CUDA(dev_alloc(&pl->counts, nslots));
+  pl->alive_words = (pl->total_syms + 31) / 32 + 1;
+  if (p->n >= pl->b + 2) {
+    PLAN_CUDA(dev_alloc(&pl->alive[0], pl->alive_words));
+    PLAN_CUDA(dev_alloc(&pl->alive[1], pl->alive_words));
+  }
+  if (pl->hot_log2) {
+    PLAN_CUDA(dev_alloc(&pl->hot, (size_t)1 << pl->hot_log2));
+    PLAN_CUDA(dev_alloc(&pl->hot_pick, (size_t)1 << pl->hot_log2));
+  }
   PLAN_CUDA(dev_alloc(&pl->table, (size_t)1 << pl->table_log2));
   PLAN_CUDA(dev_alloc(&pl->keys[0], p->candidates));
   PLAN_CUDA(dev_alloc(&pl->keys[1], p->candidates));
@@ -358,8 +382,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   PLAN_CUDA(dev_alloc(&pl->skey[0], pl->sort_cap));
   PLAN_CUDA(dev_alloc(&pl->skey[1], pl->sort_cap));
   PLAN_CUDA(dev_alloc(&pl->shist, (size_t)kSortDigits * sortG));
-  PLAN_CUDA(dev_alloc(&pl->gset, pl->gset_entries));
-  PLAN_CUDA(cudaMemsetAsync(pl->gset, 0, pl->gset_entries * sizeof(unsigned long long), pl->stream));
+  if (pl->spill_cap) PLAN_CUDA(dev_alloc(&pl->spill, (size_t)pl->scan_grid * 2 * pl->spill_cap));
   PLAN_CUDA(dev_alloc(&pl->ctl, 1));
   PLAN_CUDA(cudaMemsetAsync(pl->ctl, 0, sizeof(PassCtl), pl->stream));
   PLAN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&pl->h_ctl), sizeof(PassCtl)));

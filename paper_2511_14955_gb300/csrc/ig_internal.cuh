@@ -62,13 +62,22 @@ struct ScanArgs {
   const uint4* table;          // candidate probe table {key lo, key hi, id, 0}; null for the base pass
   uint32_t table_log2;
   uint32_t* counts;            // dense count table, indexed by slot
-  unsigned long long* gset;    // per-CTA global dedupe sets, (epoch << 32 | slot)
+  unsigned long long* gset;    // per-CTA global dedupe sets, (epoch << 32 | slot); null = spill lists
   uint32_t gset_log2;          // log2 entries of each CTA's set
+  uint32_t* spill;             // per-CTA spill list + partition buffer (2 * spill_cap words each)
+  uint64_t spill_cap;          // >= windows of the longest sequence
+  uint32_t spill_extra_log2;   // extra spill buckets (raised when a bucket overflowed)
   uint32_t count_mode;
   uint32_t words_per_thread;   // 32-bit smem words of symbols per thread per tile
   uint32_t sset_log2;          // log2 entries of the shared-memory dedupe set
   uint32_t tile_words;         // 32-bit words in the shared-memory tile buffer
   uint32_t check_overflow;     // Eq. 1 with >= 2^32 windows: detect count wrap
+  // survivor bitmasks (bit p: the window starting at corpus symbol p survived)
+  const uint32_t* alive_in;    // previous pass's survivors; null = every window is a candidate
+  uint32_t* alive_out;         // this pass's survivors; null = not needed
+  // shared-memory cache of the most frequent candidates {key lo, key hi, id, count}
+  const uint4* hot;
+  uint32_t hot_log2;           // 0 = no cache
   PassCtl* ctl;
 };
 
@@ -93,6 +102,8 @@ void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap,
 void launch_build_candidates(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
                              bool from_base, uint32_t symbol_bits, unsigned long long* keys_next,
                              uint4* table, uint32_t table_log2, cudaStream_t s);
+void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const PassCtl* ctl,
+                      uint4* hot, unsigned long long* hot_pick, uint32_t hot_log2, cudaStream_t s);
 void launch_write_topk(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
                        const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
                        uint32_t symbol_bits, uint32_t j, uint32_t row_bytes, uint32_t cap,

@@ -78,7 +78,7 @@ __device__ __forceinline__ bool seq_first_seen(uint32_t* sset, uint32_t slog, un
                                                uint32_t glog, uint32_t epoch, uint32_t slot, PassCtl* ctl) {
   const uint32_t mask = (1u << slog) - 1u;
   uint32_t h = hash32_top(slot, slog);
-  const uint32_t maxp = mask < 31u ? mask + 1u : 32u;
+  const uint32_t maxp = mask < 7u ? mask + 1u : 8u;
   for (uint32_t p = 0; p < maxp; ++p) {
     uint32_t cur = sset[h];
     if (cur == slot) return false;
@@ -92,22 +92,178 @@ __device__ __forceinline__ bool seq_first_seen(uint32_t* sset, uint32_t slog, un
   return gset_insert(gset, glog, epoch, slot, ctl);
 }
 
+// Phase 1 of the spill dedupe: bounded probe of the shared-memory set of the
+// current sequence. 0 = already present, 1 = inserted (first occurrence),
+// 2 = no room on the probe path (the slot goes to the spill list). A slot that
+// once found its path full finds it full forever (entries are never removed
+// within a sequence), so the spilled slots and the slots in the set are
+// disjoint.
+__device__ __forceinline__ int sset_try_insert(uint32_t* sset, uint32_t slog, uint32_t slot) {
+  const uint32_t mask = (1u << slog) - 1u;
+  uint32_t h = hash32_top(slot, slog);
+  const uint32_t maxp = mask < 3u ? mask + 1u : 4u;
+  for (uint32_t p = 0; p < maxp; ++p) {
+    uint32_t cur = sset[h];
+    if (cur == slot) return 0;
+    if (cur == kEmpty32) {
+      uint32_t old = atomicCAS(sset + h, kEmpty32, slot);
+      if (old == kEmpty32) return 1;
+      if (old == slot) return 0;
+    }
+    h = (h + 1) & mask;
+  }
+  return 2;
+}
+
+// Unbounded (whole-table) probe: the caller guarantees room for every
+// distinct slot it inserts; a full table is reported.
+__device__ __forceinline__ bool sset_insert_full(uint32_t* sset, uint32_t slog, uint32_t slot, PassCtl* ctl) {
+  const uint32_t mask = (1u << slog) - 1u;
+  uint32_t h = hash32_top(slot, slog);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    uint32_t cur = sset[h];
+    if (cur == slot) return false;
+    if (cur == kEmpty32) {
+      uint32_t old = atomicCAS(sset + h, kEmpty32, slot);
+      if (old == kEmpty32) return true;
+      if (old == slot) return false;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicOr(&ctl->status, kStSetFull);
+  return false;
+}
+
+// Bucket bits of a spilled slot: bits [shift, shift + kb) (from the top) of
+// the murmur3 32-bit finaliser (Appleby), unrelated to the multiply-shift
+// bits that index the shared-memory set.
+__device__ __forceinline__ uint32_t spill_bucket(uint32_t x, uint32_t shift, uint32_t kb) {
+  x ^= x >> 16; x *= 0x85ebca6bu; x ^= x >> 13; x *= 0xc2b2ae35u; x ^= x >> 16;
+  return kb == 0 ? 0u : (x << shift) >> (32 - kb);
+}
+
+__device__ __forceinline__ void register_slot(const ScanArgs& a, uint32_t slot) {
+  if (a.check_overflow) {
+    if (atomicAdd(a.counts + slot, 1u) == 0xFFFFFFFFu) atomicOr(&a.ctl->status, kStCountOverflow);
+  } else {
+    atomicAdd(a.counts + slot, 1u);
+  }
+}
+
+// Exact dedupe of src[lo, hi) in the (cleared) shared-memory set; each
+// distinct slot is registered once. Fits whenever hi - lo <= capacity / 2.
+__device__ void insert_range(const ScanArgs& a, const uint32_t* src, uint32_t lo, uint32_t hi, uint32_t* sset,
+                             unsigned long long& my_regs) {
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x, cap = 1u << a.sset_log2;
+  for (uint32_t i = tid; i < cap; i += nthr) sset[i] = kEmpty32;
+  __syncthreads();
+  for (uint32_t i = lo + tid; i < hi; i += nthr) {
+    const uint32_t v = src[i];
+    if (sset_insert_full(sset, a.sset_log2, v, a.ctl)) {
+      ++my_regs;
+      register_slot(a, v);
+    }
+  }
+  __syncthreads();
+}
+
+// Counting-sort src[lo, hi) into dst[lo, hi) by bucket bits (shift, kb);
+// bucket b ends up in dst[bnd[b], bnd[b + 1]).
+__device__ void partition_range(const uint32_t* src, uint32_t* dst, uint32_t lo, uint32_t hi, uint32_t shift,
+                                uint32_t kb, uint32_t* bnd, uint32_t* cur) {
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x, K = 1u << kb;
+  for (uint32_t b = tid; b < K; b += nthr) bnd[b] = 0;
+  __syncthreads();
+  for (uint32_t i = lo + tid; i < hi; i += nthr) atomicAdd(bnd + spill_bucket(src[i], shift, kb), 1u);
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = lo;
+    for (uint32_t b = 0; b < K; ++b) { const uint32_t c = bnd[b]; bnd[b] = run; cur[b] = run; run += c; }
+    bnd[K] = hi;
+  }
+  __syncthreads();
+  for (uint32_t i = lo + tid; i < hi; i += nthr) {
+    const uint32_t v = src[i];
+    dst[atomicAdd(cur + spill_bucket(v, shift, kb), 1u)] = v;
+  }
+  __syncthreads();
+}
+
+// smallest kb with 4n <= cap * 2^kb (expected distinct per bucket <= cap / 4)
+__device__ __forceinline__ uint32_t bucket_bits(uint32_t n, uint32_t cap, uint32_t kbmax) {
+  uint32_t kb = 0;
+  while (kb < kbmax && ((uint64_t)n << 2) > ((uint64_t)cap << kb)) ++kb;
+  return kb;
+}
+
+// Phase 2: the spilled slots of one sequence (S entries, duplicates
+// included, disjoint from the slots already in the set) are hash-partitioned
+// (at most two levels, bucket tables in the free tile buffer) into buckets of
+// at most half the set's capacity, and each bucket is deduplicated exactly.
+__device__ void dedupe_spills(const ScanArgs& a, uint32_t S, uint32_t* sset, uint32_t* scratch,
+                              uint32_t scratch_words, uint32_t* list, uint32_t* part,
+                              unsigned long long& my_regs) {
+  const uint32_t cap = 1u << a.sset_log2, fit = cap / 2;
+  if (S <= fit) {
+    insert_range(a, list, 0, S, sset, my_regs);
+    return;
+  }
+  const uint32_t half = scratch_words / 2;
+  uint32_t kbmax = 0;
+  while (kbmax < 12 && (2u << (kbmax + 1)) + 1 <= half) ++kbmax;
+  uint32_t* bnd1 = scratch;
+  uint32_t* bnd2 = scratch + half;
+  const uint32_t kb1 = bucket_bits(S, cap, kbmax) + a.spill_extra_log2 > kbmax
+                           ? kbmax : bucket_bits(S, cap, kbmax) + a.spill_extra_log2;
+  const uint32_t K1 = 1u << kb1;
+  partition_range(list, part, 0, S, 0, kb1, bnd1, bnd1 + K1 + 1);
+  for (uint32_t b1 = 0; b1 < K1; ++b1) {
+    const uint32_t lo = bnd1[b1], hi = bnd1[b1 + 1];
+    if (hi == lo) continue;  // uniform across the CTA
+    if (hi - lo <= fit) {
+      insert_range(a, part, lo, hi, sset, my_regs);
+      continue;
+    }
+    const uint32_t kb2 = bucket_bits(hi - lo, cap, kbmax);
+    const uint32_t K2 = 1u << kb2;
+    partition_range(part, list, lo, hi, kb1, kb2, bnd2, bnd2 + K2 + 1);
+    for (uint32_t b2 = 0; b2 < K2; ++b2) {
+      const uint32_t l2 = bnd2[b2], h2 = bnd2[b2 + 1];
+      if (h2 > l2) insert_range(a, list, l2, h2, sset, my_regs);
+    }
+  }
+}
+
 template <int SB, bool BASE>
 __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_item, s_nspill;
   __shared__ unsigned long long s_surv, s_regs;
 
   using S = Sym<SB>;
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
   const uint32_t R = a.words_per_thread * S::kPerWord;  // windows per thread per tile
   const uint32_t tile_windows = R * nthr;
+  const uint32_t H = (BASE || a.hot_log2 == 0) ? 0u : (1u << a.hot_log2);
+  // shared memory: [dedupe set][hot keys][hot ids][tile]
   uint32_t* sset = smem;
-  uint32_t* tile = smem + (1u << a.sset_log2);
+  unsigned long long* hot_keys = reinterpret_cast<unsigned long long*>(smem + (1u << a.sset_log2));
+  uint32_t* hot_ids = reinterpret_cast<uint32_t*>(hot_keys + H);
+  uint32_t* tile = hot_ids + H;
   uint8_t* tile_b = reinterpret_cast<uint8_t*>(tile);
-  unsigned long long* gset = a.gset + ((unsigned long long)blockIdx.x << a.gset_log2);
+  unsigned long long* gset = a.gset ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
+  // CTA-private spill list and partition buffer (Eq. 2 without a global set)
+  uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
+  uint32_t* spill_part = spill_list ? spill_list + a.spill_cap : nullptr;
   const uint32_t j = a.j;
   const uint32_t epoch_base = a.ctl->epoch_base;
+
+  // the most frequent candidates, cached in shared memory in front of the table
+  for (uint32_t i = tid; i < H; i += nthr) {
+    const uint4 e = a.hot[i];
+    hot_keys[i] = ((unsigned long long)e.y << 32) | e.x;
+    hot_ids[i] = e.z;
+  }
 
   unsigned long long my_surv = 0, my_regs = 0;
   if (tid == 0) { s_surv = 0; s_regs = 0; }
@@ -133,6 +289,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
       if (glog < 1) glog = 1;
       for (uint32_t i = tid; i < (1u << slog); i += nthr) sset[i] = kEmpty32;
     }
+    if (tid == 0) s_nspill = 0;
 
     for (uint64_t w0 = 0; w0 < W; w0 += tile_windows) {
       const uint32_t nwin = (uint32_t)((W - w0) < tile_windows ? (W - w0) : tile_windows);
@@ -175,6 +332,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
         uint32_t word = bswap32(tile[widx]);
         uint64_t key = 0;
         const uint32_t total = (we - wb) + j - 1;
+        // survivor bitmasks, indexed by the window's first symbol in the corpus
+        const uint64_t gp0 = gsym + wb;
+        uint64_t in_idx = ~0ull, out_idx = ~0ull;
+        uint32_t in_word = 0xFFFFFFFFu, out_word = 0;
         for (uint32_t i = 0; i < total; ++i) {
           const uint32_t sym = (word >> (32 - SB * (q + 1))) & S::kMask;
           if (++q == S::kPerWord) {
@@ -184,28 +345,59 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           }
           key = ((key << SB) | sym) & a.key_mask;
           if (i + 1 < j) continue;
+          const uint64_t gp = gp0 + (i + 1 - j);
           uint32_t slot;
           if (BASE) {
             slot = (uint32_t)key;
           } else {
-            const uint32_t id = probe_table(a.table, a.table_log2, key >> SB, a.ctl);
+            if (a.alive_in) {
+              if ((gp >> 5) != in_idx) {
+                in_idx = gp >> 5;
+                in_word = __ldg(a.alive_in + in_idx);
+              }
+              if (!((in_word >> (gp & 31)) & 1u)) continue;
+            }
+            const uint64_t prefix = key >> SB;
+            uint32_t id = kEmpty32;
+            if (H) {
+              const uint32_t h = hash64_top(prefix, a.hot_log2);
+              if (hot_keys[h] == prefix) id = hot_ids[h];
+            }
+            if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
             if (id == kEmpty32) continue;
             slot = (id << SB) | (uint32_t)(key & S::kMask);
+            if (a.alive_out) {
+              if ((gp >> 5) != out_idx) {
+                if (out_word) atomicOr(a.alive_out + out_idx, out_word);
+                out_idx = gp >> 5;
+                out_word = 0;
+              }
+              out_word |= 1u << (gp & 31);
+            }
           }
           ++my_surv;
           bool count_it = true;
-          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE)
-            count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
-          if (count_it) {
-            ++my_regs;
-            if (a.check_overflow) {
-              if (atomicAdd(a.counts + slot, 1u) == 0xFFFFFFFFu) atomicOr(&a.ctl->status, kStCountOverflow);
+          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+            if (spill_list) {
+              const int r = sset_try_insert(sset, slog, slot);
+              count_it = (r == 1);
+              if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
             } else {
-              atomicAdd(a.counts + slot, 1u);
+              count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
             }
           }
+          if (count_it) {
+            ++my_regs;
+            register_slot(a, slot);
+          }
         }
+        if (out_word) atomicOr(a.alive_out + out_idx, out_word);
       }
+      __syncthreads();
+    }
+    if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+      const uint32_t nsp = s_nspill;  // read after the tile loop's final barrier
+      if (nsp) dedupe_spills(a, nsp, sset, tile, a.tile_words, spill_list, spill_part, my_regs);
       __syncthreads();
     }
   }

@@ -67,7 +67,47 @@ __global__ void write_topk_kernel(const uint32_t* sel_slot, const uint32_t* sel_
   }
 }
 
+// Hot cache of P^(j): a direct-mapped table in which each bucket keeps the
+// candidate with the highest count (lowest id on ties) among those hashing
+// to it. It only caches exact (key, id) pairs, so its content never changes
+// a result.
+__global__ void hot_clear_kernel(uint4* hot, unsigned long long* pick, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    hot[i] = make_uint4(0u, 0u, kEmpty32, 0u);
+    pick[i] = 0ull;
+  }
+}
+
+__global__ void hot_pick_kernel(const unsigned long long* keys, const uint32_t* sel_count, const PassCtl* ctl,
+                                unsigned long long* pick, uint32_t log2) {
+  const uint32_t n = ctl->nsel;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const uint32_t h = hash64_top(keys[r], log2);
+    atomicMax(pick + h, ((unsigned long long)sel_count[r] << 32) | (0xFFFFFFFFu - r));
+  }
+}
+
+__global__ void hot_fill_kernel(const unsigned long long* keys, const unsigned long long* pick, uint4* hot,
+                                uint32_t n) {
+  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+    const unsigned long long v = pick[h];
+    if (!v) continue;
+    const uint32_t r = 0xFFFFFFFFu - (uint32_t)v;
+    const unsigned long long key = keys[r];
+    hot[h] = make_uint4((uint32_t)key, (uint32_t)(key >> 32), r, (uint32_t)(v >> 32));
+  }
+}
+
 }  // namespace
+
+void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const PassCtl* ctl, uint4* hot,
+                      unsigned long long* hot_pick, uint32_t hot_log2, cudaStream_t s) {
+  const uint32_t n = 1u << hot_log2;
+  const int g = (int)((n + 255) / 256);
+  hot_clear_kernel<<<g, 256, 0, s>>>(hot, hot_pick, n);
+  hot_pick_kernel<<<512, 256, 0, s>>>(keys, sel_count, ctl, hot_pick, hot_log2);
+  hot_fill_kernel<<<g, 256, 0, s>>>(keys, hot_pick, hot, n);
+}
 
 void launch_build_candidates(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
                              bool from_base, uint32_t symbol_bits, unsigned long long* keys_next, uint4* table,
