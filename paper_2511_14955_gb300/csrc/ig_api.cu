@@ -98,6 +98,7 @@ struct ig_plan {
   int scan_grid = 0, scan_threads = 512;
   size_t scan_smem = 0;
   uint32_t tile_words = 0;
+  uint32_t queue_words = 0;
 
   uint8_t* out_keys = nullptr;
   unsigned long long* out_counts = nullptr;
@@ -180,6 +181,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.words_per_thread = pl->t.words_per_thread;
   a.sset_log2 = pl->t.smem_set_log2;
   a.tile_words = pl->tile_words;
+  a.queue_words = pl->queue_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
   // pass j reads the survivors of pass j-1 (written by candidate passes only)
   // and writes its own when pass j+1 will read them
@@ -315,9 +317,10 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   // tuning (defaults; the autotuner in the binding may override)
   ig_tuning t{};
   if (tuning) t = *tuning;
+  const bool auto_set = (t.smem_set_log2 == 0);
   if (!t.ctas_per_sm) t.ctas_per_sm = 1;
   if (!t.threads) t.threads = 1024;
-  if (!t.words_per_thread) t.words_per_thread = 9;
+  if (!t.words_per_thread) t.words_per_thread = p->symbol_bits == 8 ? 5 : 3;
   if (!t.smem_set_log2) t.smem_set_log2 = 15;
   if (!t.table_load_pct) t.table_load_pct = 25;
   if (!t.hot_log2) t.hot_log2 = 11;
@@ -341,15 +344,30 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   // Eq. 1 with 2^32 or more windows can overflow a 32-bit count
   pl->check_overflow = p->count_mode == IG_COUNT_EVERY_OCCURRENCE && pl->total_syms >= 0xFFFFFFFFull;
 
-  // scan launch geometry
+  // scan launch geometry: shared memory = dedupe set + hot cache + tile (with
+  // halo and alignment slop) + candidate queue (2 bytes per tile window) +
+  // the tile's survivor bits. Tiles are capped at 65536 windows (16-bit
+  // queue entries).
   const uint32_t spw = 32 / pl->sb;
-  const uint64_t tile_syms = (uint64_t)t.words_per_thread * spw * t.threads + p->n + 2 * 16 * (8 / pl->sb);
+  if ((uint64_t)t.words_per_thread * spw * t.threads > 65536)
+    return bail(fail(IG_EINVAL, "tile too large: threads * words_per_thread * symbols per word must be <= 65536"));
+  pl->hot_log2 = (pl->b < p->n) ? t.hot_log2 : 0u;
+  const uint64_t tile_windows = (uint64_t)t.words_per_thread * spw * t.threads;
+  const uint64_t tile_syms = tile_windows + p->n + 2 * 16 * (8 / pl->sb);
   pl->tile_words = (uint32_t)((tile_syms * pl->sb + 31) / 32) + 8;
   pl->tile_words = (pl->tile_words + 3) & ~3u;
+  pl->queue_words = (uint32_t)(((tile_windows + 1) / 2 + 3) & ~3ull);
+  const uint32_t alive_tile_words = (uint32_t)((tile_windows + 31) / 32);
+  auto smem_for = [&](uint32_t set_log2) {
+    return ((size_t)4 << set_log2) + (size_t)12 * (pl->hot_log2 ? (1u << pl->hot_log2) : 0u) +
+           (size_t)4 * (pl->tile_words + pl->queue_words + alive_tile_words);
+  };
+  int max_optin = 0;
+  PLAN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+  while (auto_set && t.smem_set_log2 > 8 && smem_for(t.smem_set_log2) + 256 > (size_t)max_optin) --t.smem_set_log2;
+  pl->t = t;
   pl->scan_threads = (int)t.threads;
-  pl->hot_log2 = (pl->b < p->n) ? t.hot_log2 : 0u;
-  pl->scan_smem = ((size_t)4 << t.smem_set_log2) + (size_t)12 * (pl->hot_log2 ? (1u << pl->hot_log2) : 0u) +
-                  (size_t)pl->tile_words * 4;
+  pl->scan_smem = smem_for(t.smem_set_log2);
   for (bool base : {true, false}) PLAN_CUDA(scan_set_smem_limit(pl->sb, base, pl->scan_smem));
   int occ = std::min(scan_max_ctas_per_sm(pl->sb, false, pl->scan_threads, pl->scan_smem),
                      scan_max_ctas_per_sm(pl->sb, true, pl->scan_threads, pl->scan_smem));

@@ -71,6 +71,7 @@ struct ScanArgs {
   uint32_t words_per_thread;   // 32-bit smem words of symbols per thread per tile
   uint32_t sset_log2;          // log2 entries of the shared-memory dedupe set
   uint32_t tile_words;         // 32-bit words in the shared-memory tile buffer
+  uint32_t queue_words;        // 32-bit words of the candidate queue (2 bytes per tile window) + survivor bits
   uint32_t check_overflow;     // Eq. 1 with >= 2^32 windows: detect count wrap
   // survivor bitmasks (bit p: the window starting at corpus symbol p survived)
   const uint32_t* alive_in;    // previous pass's survivors; null = every window is a candidate

@@ -92,6 +92,19 @@ __device__ __forceinline__ bool seq_first_seen(uint32_t* sset, uint32_t slog, un
   return gset_insert(gset, glog, epoch, slot, ctl);
 }
 
+// Key of the window whose first symbol is tile symbol `o` (j * SB <= 64 bits):
+// 64 bits of the (big-endian) symbol stream starting at bit o * SB, shifted
+// down to j symbols. Reads three words; the tile buffer has slack past its end.
+template <int SB>
+__device__ __forceinline__ uint64_t tile_key(const uint32_t* tile, uint32_t o, uint32_t j) {
+  const uint32_t bit = o * SB, wi = bit >> 5, sh = bit & 31;
+  const uint64_t hi = ((uint64_t)__byte_perm(tile[wi], 0, 0x0123) << 32) | __byte_perm(tile[wi + 1], 0, 0x0123);
+  const uint32_t w2 = __byte_perm(tile[wi + 2], 0, 0x0123);
+  const uint64_t v = sh ? ((hi << sh) | (w2 >> (32 - sh))) : hi;
+  const uint32_t bits = j * SB;
+  return bits >= 64 ? v : (v >> (64 - bits));
+}
+
 // Phase 1 of the spill dedupe: bounded probe of the shared-memory set of the
 // current sequence. 0 = already present, 1 = inserted (first occurrence),
 // 2 = no room on the probe path (the slot goes to the spill list). A slot that
@@ -237,7 +250,7 @@ __device__ void dedupe_spills(const ScanArgs& a, uint32_t S, uint32_t* sset, uin
 template <int SB, bool BASE>
 __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_item, s_nspill;
+  __shared__ uint32_t s_item, s_nspill, s_qn;
   __shared__ unsigned long long s_surv, s_regs;
 
   using S = Sym<SB>;
@@ -251,6 +264,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   uint32_t* hot_ids = reinterpret_cast<uint32_t*>(hot_keys + H);
   uint32_t* tile = hot_ids + H;
   uint8_t* tile_b = reinterpret_cast<uint8_t*>(tile);
+  // candidate passes: queue of alive windows (tile-relative indices) and the
+  // tile's survivor bits
+  uint16_t* queue = reinterpret_cast<uint16_t*>(tile + a.tile_words);
+  uint32_t* tile_alive = tile + a.tile_words + a.queue_words;
+  const uint32_t alive_tile_words = (tile_windows + 31) / 32;
   unsigned long long* gset = a.gset ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
   // CTA-private spill list and partition buffer (Eq. 2 without a global set)
   uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
@@ -325,56 +343,93 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
       __syncthreads();
 
       const uint32_t wb = tid * R;
-      if (wb < nwin) {
-        const uint32_t we = (wb + R) < nwin ? (wb + R) : nwin;
-        uint32_t s = sym_off + wb;
-        uint32_t widx = s / S::kPerWord, q = s % S::kPerWord;
-        uint32_t word = bswap32(tile[widx]);
-        uint64_t key = 0;
-        const uint32_t total = (we - wb) + j - 1;
-        // survivor bitmasks, indexed by the window's first symbol in the corpus
-        const uint64_t gp0 = gsym + wb;
-        uint64_t in_idx = ~0ull, out_idx = ~0ull;
-        uint32_t in_word = 0xFFFFFFFFu, out_word = 0;
-        for (uint32_t i = 0; i < total; ++i) {
-          const uint32_t sym = (word >> (32 - SB * (q + 1))) & S::kMask;
-          if (++q == S::kPerWord) {
-            q = 0;
-            ++widx;
-            word = (widx < a.tile_words) ? bswap32(tile[widx]) : 0u;
-          }
-          key = ((key << SB) | sym) & a.key_mask;
-          if (i + 1 < j) continue;
-          const uint64_t gp = gp0 + (i + 1 - j);
-          uint32_t slot;
-          if (BASE) {
-            slot = (uint32_t)key;
-          } else {
-            if (a.alive_in) {
-              if ((gp >> 5) != in_idx) {
-                in_idx = gp >> 5;
-                in_word = __ldg(a.alive_in + in_idx);
-              }
-              if (!((in_word >> (gp & 31)) & 1u)) continue;
+      if (BASE) {
+        if (wb < nwin) {
+          const uint32_t we = (wb + R) < nwin ? (wb + R) : nwin;
+          uint32_t s = sym_off + wb;
+          uint32_t widx = s / S::kPerWord, q = s % S::kPerWord;
+          uint32_t word = bswap32(tile[widx]);
+          uint64_t key = 0;
+          const uint32_t total = (we - wb) + j - 1;
+          for (uint32_t i = 0; i < total; ++i) {
+            const uint32_t sym = (word >> (32 - SB * (q + 1))) & S::kMask;
+            if (++q == S::kPerWord) {
+              q = 0;
+              ++widx;
+              word = (widx < a.tile_words) ? bswap32(tile[widx]) : 0u;
             }
-            const uint64_t prefix = key >> SB;
-            uint32_t id = kEmpty32;
-            if (H) {
-              const uint32_t h = hash64_top(prefix, a.hot_log2);
-              if (hot_keys[h] == prefix) id = hot_ids[h];
-            }
-            if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
-            if (id == kEmpty32) continue;
-            slot = (id << SB) | (uint32_t)(key & S::kMask);
-            if (a.alive_out) {
-              if ((gp >> 5) != out_idx) {
-                if (out_word) atomicOr(a.alive_out + out_idx, out_word);
-                out_idx = gp >> 5;
-                out_word = 0;
+            key = ((key << SB) | sym) & a.key_mask;
+            if (i + 1 < j) continue;
+            const uint32_t slot = (uint32_t)key;
+            ++my_surv;
+            bool count_it = true;
+            if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+              if (spill_list) {
+                const int r = sset_try_insert(sset, slog, slot);
+                count_it = (r == 1);
+                if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+              } else {
+                count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
               }
-              out_word |= 1u << (gp & 31);
+            }
+            if (count_it) {
+              ++my_regs;
+              register_slot(a, slot);
             }
           }
+        }
+      } else {
+        // phase A: every thread walks its run of windows; alive ones are
+        // queued (warp-aggregated), so phase B can process them densely
+        if (tid == 0) s_qn = 0;
+        if (a.alive_out)
+          for (uint32_t i = tid; i < alive_tile_words; i += nthr) tile_alive[i] = 0;
+        __syncthreads();
+        const uint32_t lane = tid & 31;
+        const uint32_t total = wb < nwin ? ((wb + R < nwin ? R : nwin - wb) + j - 1) : 0u;
+        if (a.alive_in) {
+          uint32_t in_idx = 0xFFFFFFFFu, in_word = 0;
+          for (uint32_t i = j - 1; i < R + j - 1; ++i) {
+            bool cand = false;
+            uint32_t w = 0;
+            if (i < total) {
+              w = wb + i + 1 - j;
+              const uint64_t gp = gsym + w;
+              if ((uint32_t)(gp >> 5) != in_idx) {
+                in_idx = (uint32_t)(gp >> 5);
+                in_word = __ldg(a.alive_in + (gp >> 5));
+              }
+              cand = (in_word >> (gp & 31)) & 1u;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, cand);
+            if (m) {
+              uint32_t base = 0;
+              if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(&s_qn, (uint32_t)__popc(m));
+              base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+              if (cand) queue[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
+            }
+          }
+        } else {
+          // no survivor mask: every window of the tile is a candidate
+          for (uint32_t w = tid; w < nwin; w += nthr) queue[w] = (uint16_t)w;
+          if (tid == 0) s_qn = nwin;
+        }
+        __syncthreads();
+        // phase B: probe, count, dedupe the queued windows
+        const uint32_t qn = s_qn;
+        for (uint32_t qi = tid; qi < qn; qi += nthr) {
+          const uint32_t w = queue[qi];
+          const uint64_t key = tile_key<SB>(tile, sym_off + w, j);
+          const uint64_t prefix = key >> SB;
+          uint32_t id = kEmpty32;
+          if (H) {
+            const uint32_t h = hash64_top(prefix, a.hot_log2);
+            if (hot_keys[h] == prefix) id = hot_ids[h];
+          }
+          if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
+          if (id == kEmpty32) continue;
+          const uint32_t slot = (id << SB) | (uint32_t)(key & S::kMask);
+          if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
           ++my_surv;
           bool count_it = true;
           if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
@@ -391,13 +446,25 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             register_slot(a, slot);
           }
         }
-        if (out_word) atomicOr(a.alive_out + out_idx, out_word);
+        if (a.alive_out) {
+          __syncthreads();
+          // tile bit w is corpus bit gsym + w
+          const uint32_t off = (uint32_t)(gsym & 31);
+          const uint64_t g0 = gsym >> 5;
+          const uint32_t nw = (nwin + off + 31) / 32;
+          for (uint32_t k = tid; k < nw; k += nthr) {
+            const uint32_t cur = k < alive_tile_words ? tile_alive[k] : 0u;
+            const uint32_t prev = (k > 0 && off) ? tile_alive[k - 1] : 0u;
+            const uint32_t v = off ? ((cur << off) | (prev >> (32 - off))) : cur;
+            if (v) atomicOr(a.alive_out + g0 + k, v);
+          }
+        }
       }
       __syncthreads();
     }
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       const uint32_t nsp = s_nspill;  // read after the tile loop's final barrier
-      if (nsp) dedupe_spills(a, nsp, sset, tile, a.tile_words, spill_list, spill_part, my_regs);
+      if (nsp) dedupe_spills(a, nsp, sset, tile, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
       __syncthreads();
     }
   }

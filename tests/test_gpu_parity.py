@@ -84,7 +84,7 @@ def test_dna_reduced(mode):
 
 @pytest.mark.parametrize("tuning", [
     dict(threads=256, words_per_thread=1, smem_set_log2=8, ctas_per_sm=4),   # tiny tiles, heavy spill
-    dict(threads=1024, words_per_thread=13, smem_set_log2=15, ctas_per_sm=1),
+    dict(threads=1024, words_per_thread=7, smem_set_log2=14, ctas_per_sm=1),
     dict(threads=512, words_per_thread=3, smem_set_log2=10, table_load_pct=50, hot_log2=6),
     dict(threads=512, words_per_thread=5, smem_set_log2=12, hot_log2=13),
 ])
