@@ -79,6 +79,7 @@ struct ig_plan {
   int cur = 0;             // keys[cur] = keys of the latest candidate set
   uint32_t* sel_slot = nullptr;
   uint32_t* sel_count = nullptr;
+  uint32_t* rank = nullptr;          // rank of each candidate id (counter row of the next scan)
   uint32_t* hist = nullptr;
   uint32_t* blk = nullptr;
   int G = 1024;
@@ -137,7 +138,7 @@ void release(ig_plan* pl) {
   void* ptrs[] = {pl->own_data, pl->own_offsets, pl->counts, pl->table, pl->keys[0], pl->keys[1],
                   pl->sel_slot, pl->sel_count, pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
-                  pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick};
+                  pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
@@ -198,15 +199,23 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   }
   if (timing) cudaEventRecordWithFlags(pl->ev_scan1[ti], s, evf);
   const uint32_t target = (j < pl->p.n) ? pl->p.candidates : pl->p.k;
-  launch_select(pl->counts, ns, target, pl->ctl, pl->hist, pl->blk, pl->G, pl->sel_slot, pl->sel_count, s);
+  // the scan of a candidate pass counted in rank space; selection reads the
+  // counters back in byte order through the rank map
+  launch_select(pl->counts, base ? nullptr : pl->rank, pl->sb, ns, target, pl->ctl, pl->hist, pl->blk, pl->G,
+                pl->sel_slot, pl->sel_count, s);
   kernels += 12;
   if (j < pl->p.n) {
     const int nxt = pl->cur ^ 1;
-    launch_build_candidates(pl->sel_slot, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], pl->table,
-                            pl->table_log2, s);
-    kernels += 2;
+    // P^(j): keys in byte order, then ranks by (count desc, id asc) for the
+    // next scan's counters, then the probe table and hot cache (key -> rank)
+    launch_build_keys(pl->sel_slot, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], s);
+    launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
+                         pl->shist, s);
+    launch_rank(pl->sidx[0], pl->ctl, pl->rank, pl->p.candidates, s);
+    launch_build_table(pl->keys[nxt], pl->rank, pl->ctl, pl->table, pl->table_log2, s);
+    kernels += 1 + 13 + 2 + 2;
     if (pl->hot_log2) {
-      launch_build_hot(pl->keys[nxt], pl->sel_count, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
+      launch_build_hot(pl->keys[nxt], pl->sel_count, pl->rank, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
       kernels += 3;
     }
   }
@@ -393,6 +402,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   PLAN_CUDA(dev_alloc(&pl->keys[1], p->candidates));
   PLAN_CUDA(dev_alloc(&pl->sel_slot, p->candidates));
   PLAN_CUDA(dev_alloc(&pl->sel_count, p->candidates));
+  PLAN_CUDA(dev_alloc(&pl->rank, p->candidates));
   PLAN_CUDA(dev_alloc(&pl->hist, (size_t)kMaxLevels * kHistBins));
   PLAN_CUDA(dev_alloc(&pl->blk, (size_t)2 * pl->G));
   PLAN_CUDA(dev_alloc(&pl->sidx[0], pl->sort_cap));

@@ -92,19 +92,27 @@ cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t s
 
 // Launchers (ig_select.cu)
 void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint64_t gset_entries, cudaStream_t s);
-void launch_select(const uint32_t* counts, uint64_t ns, uint32_t target, PassCtl* ctl,
-                   uint32_t* hist /* kMaxLevels*kHistBins */, uint32_t* blk /* 2*G */, int G,
+// rank: null for the dense base pass; otherwise the counter of slot id*sigma+sym is
+// at rank[id]*sigma+sym (candidate passes count in rank space)
+void launch_select(const uint32_t* counts, const uint32_t* rank, uint32_t sb, uint64_t ns, uint32_t target,
+                   PassCtl* ctl, uint32_t* hist /* kMaxLevels*kHistBins */, uint32_t* blk /* 2*G */, int G,
                    uint32_t* sel_slot, uint32_t* sel_count, cudaStream_t s);
+// rank[order[x]] = x for the nsel selected candidates, rank[i] = i beyond
+void launch_rank(const uint32_t* order, const PassCtl* ctl, uint32_t* rank, uint32_t n, cudaStream_t s);
 void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap,
                           uint32_t* idx_a, uint32_t* idx_b, uint32_t* key_a, uint32_t* key_b,
                           uint32_t* hist /* kSortDigits * ceil(cap/kSortChunk) */, cudaStream_t s);
 
 // Launchers (ig_table.cu)
-void launch_build_candidates(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
-                             bool from_base, uint32_t symbol_bits, unsigned long long* keys_next,
-                             uint4* table, uint32_t table_log2, cudaStream_t s);
-void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const PassCtl* ctl,
-                      uint4* hot, unsigned long long* hot_pick, uint32_t hot_log2, cudaStream_t s);
+// keys_next[r] = key of selected slot r; ids are in byte order
+void launch_build_keys(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
+                       bool from_base, uint32_t symbol_bits, unsigned long long* keys_next, cudaStream_t s);
+// probe table: key -> rank[r] (the counter row the next scan uses)
+void launch_build_table(const unsigned long long* keys, const uint32_t* rank, const PassCtl* ctl, uint4* table,
+                        uint32_t table_log2, cudaStream_t s);
+void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const uint32_t* rank,
+                      const PassCtl* ctl, uint4* hot, unsigned long long* hot_pick, uint32_t hot_log2,
+                      cudaStream_t s);
 void launch_write_topk(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
                        const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
                        uint32_t symbol_bits, uint32_t j, uint32_t row_bytes, uint32_t cap,

@@ -154,14 +154,23 @@ __global__ void level_pick_kernel(PassCtl* ctl, uint32_t* hist) {
 }
 
 // Stable compaction, phase 1: per-block numbers of counters > thr and == thr.
-__global__ void compact_count_kernel(const uint32_t* __restrict__ c, uint64_t ns, const PassCtl* ctl,
-                                     uint32_t* blk, uint64_t chunk) {
+// Counter of slot s (byte order). Candidate passes count in rank space:
+// slot id * sigma + sym lives at rank[id] * sigma + sym.
+__device__ __forceinline__ uint32_t counter_of(const uint32_t* __restrict__ c, const uint32_t* __restrict__ rank,
+                                               uint32_t sb, uint64_t s) {
+  if (!rank) return c[s];
+  const uint64_t id = s >> sb;
+  return c[((uint64_t)rank[id] << sb) | (s & ((1u << sb) - 1u))];
+}
+
+__global__ void compact_count_kernel(const uint32_t* __restrict__ c, const uint32_t* __restrict__ rank, uint32_t sb,
+                                     uint64_t ns, const PassCtl* ctl, uint32_t* blk, uint64_t chunk) {
   const uint32_t thr = ctl->thr;
   const bool eq_used = !ctl->take_all;
   const uint64_t b0 = blockIdx.x * chunk, b1 = min(ns, b0 + chunk);
   uint32_t gt = 0, eq = 0;
   for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    uint32_t v = c[i];
+    uint32_t v = counter_of(c, rank, sb, i);
     gt += v > thr;
     eq += eq_used && v == thr;
   }
@@ -235,8 +244,9 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_t
 }
 
 // Phase 3: write the selected (slot, count) pairs in slot order.
-__global__ void compact_write_kernel(const uint32_t* __restrict__ c, uint64_t ns, const PassCtl* ctl,
-                                     const uint32_t* blk, uint64_t chunk, uint32_t* sel_slot, uint32_t* sel_count) {
+__global__ void compact_write_kernel(const uint32_t* __restrict__ c, const uint32_t* __restrict__ rank, uint32_t sb,
+                                     uint64_t ns, const PassCtl* ctl, const uint32_t* blk, uint64_t chunk,
+                                     uint32_t* sel_slot, uint32_t* sel_count) {
   __shared__ uint32_t wt[33];
   const uint32_t thr = ctl->thr, need = ctl->need_eq;
   const bool eq_used = !ctl->take_all;
@@ -244,7 +254,7 @@ __global__ void compact_write_kernel(const uint32_t* __restrict__ c, uint64_t ns
   uint32_t base_gt = blk[2 * blockIdx.x], base_eq = blk[2 * blockIdx.x + 1];
   for (uint64_t t0 = b0; t0 < b1; t0 += blockDim.x) {
     uint64_t i = t0 + threadIdx.x;
-    uint32_t v = i < b1 ? c[i] : 0u;
+    uint32_t v = i < b1 ? counter_of(c, rank, sb, i) : 0u;
     uint32_t gt = v > thr, eq = eq_used && i < b1 && v == thr;
     uint32_t tg, te;
     uint32_t rg = block_excl_scan(gt, wt, tg);
@@ -328,7 +338,24 @@ __global__ void sort_scatter_kernel(const uint32_t* key_in, const uint32_t* idx_
   }
 }
 
+// rank[id] = id: ids beyond the candidate set then map to counters that are
+// never incremented (they read as zero).
+__global__ void rank_init_kernel(uint32_t* rank, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) rank[i] = i;
+}
+
+// order[x] = id of the x-th candidate by (count desc, id asc)  ->  rank[id] = x
+__global__ void rank_scatter_kernel(const uint32_t* order, const PassCtl* ctl, uint32_t* rank) {
+  const uint32_t n = ctl->nsel;
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) rank[order[x]] = x;
+}
+
 }  // namespace
+
+void launch_rank(const uint32_t* order, const PassCtl* ctl, uint32_t* rank, uint32_t n, cudaStream_t s) {
+  rank_init_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(rank, n);
+  rank_scatter_kernel<<<256, 256, 0, s>>>(order, ctl, rank);
+}
 
 void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint64_t gset_entries, cudaStream_t s) {
   pass_reset_kernel<<<1, 32, 0, s>>>(ctl, m);
@@ -338,8 +365,9 @@ void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint6
   }
 }
 
-void launch_select(const uint32_t* counts, uint64_t ns, uint32_t target, PassCtl* ctl, uint32_t* hist,
-                   uint32_t* blk, int G, uint32_t* sel_slot, uint32_t* sel_count, cudaStream_t s) {
+void launch_select(const uint32_t* counts, const uint32_t* rank, uint32_t sb, uint64_t ns, uint32_t target,
+                   PassCtl* ctl, uint32_t* hist, uint32_t* blk, int G, uint32_t* sel_slot, uint32_t* sel_count,
+                   cudaStream_t s) {
   sel_reset_kernel<<<1, 1024, 0, s>>>(ctl, target, hist);
   int grid = 4 * 152;
   max_nonzero_kernel<<<grid, kThreads, 0, s>>>(counts, ns, ctl);
@@ -351,9 +379,9 @@ void launch_select(const uint32_t* counts, uint64_t ns, uint32_t target, PassCtl
   uint64_t chunk = (ns + G - 1) / G;
   chunk = (chunk + 255) & ~255ull;
   if (chunk == 0) chunk = 256;
-  compact_count_kernel<<<G, kThreads, 0, s>>>(counts, ns, ctl, blk, chunk);
+  compact_count_kernel<<<G, kThreads, 0, s>>>(counts, rank, sb, ns, ctl, blk, chunk);
   compact_scan_kernel<<<1, 1024, 0, s>>>(blk, G);
-  compact_write_kernel<<<G, kThreads, 0, s>>>(counts, ns, ctl, blk, chunk, sel_slot, sel_count);
+  compact_write_kernel<<<G, kThreads, 0, s>>>(counts, rank, sb, ns, ctl, blk, chunk, sel_slot, sel_count);
 }
 
 void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap, uint32_t* idx_a,

@@ -7,7 +7,9 @@
 // dense base pass the slot is the j-gram itself). Keys are right-aligned
 // integers of j * symbol_bits <= 64 bits, so integer order is byte order.
 //
-// The probe table maps a key to its id: open addressing with linear probing
+// The next scan counts in rank space (candidates renumbered by count, hottest
+// first, so the counters it hits most are packed together): the probe table
+// maps a key to its rank: open addressing with linear probing
 // over 16-byte entries {key low, key high, id, 0}, multiply-shift hashed,
 // kept at or below the configured load so that lookups (one per window in the
 // next scan) touch about one 32-byte sector.
@@ -28,18 +30,24 @@ __device__ __forceinline__ unsigned long long key_of_slot(uint32_t slot, const u
   return (keys_prev[slot >> sb] << sb) | (slot & ((1u << sb) - 1u));
 }
 
-__global__ void build_kernel(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
-                             bool from_base, uint32_t sb, unsigned long long* keys_next, uint4* table,
+__global__ void keys_kernel(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
+                            bool from_base, uint32_t sb, unsigned long long* keys_next) {
+  const uint32_t n = ctl->nsel;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    keys_next[r] = key_of_slot(sel_slot[r], keys_prev, from_base, sb);
+}
+
+__global__ void build_kernel(const unsigned long long* keys, const uint32_t* rank, const PassCtl* ctl, uint4* table,
                              uint32_t log2, PassCtl* ctl_w) {
   const uint32_t n = ctl->nsel, mask = (1u << log2) - 1u;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const unsigned long long key = key_of_slot(sel_slot[r], keys_prev, from_base, sb);
-    keys_next[r] = key;
+    const unsigned long long key = keys[r];
+    const uint32_t val = rank[r];
     uint32_t h = hash64_top(key, log2);
     bool placed = false;
     for (uint32_t it = 0; it <= mask; ++it) {
       uint32_t* idp = &table[h].z;
-      if (atomicCAS(idp, kEmpty32, r) == kEmpty32) {
+      if (atomicCAS(idp, kEmpty32, val) == kEmpty32) {
         table[h].x = (uint32_t)key;
         table[h].y = (uint32_t)(key >> 32);
         placed = true;
@@ -87,35 +95,39 @@ __global__ void hot_pick_kernel(const unsigned long long* keys, const uint32_t* 
   }
 }
 
-__global__ void hot_fill_kernel(const unsigned long long* keys, const unsigned long long* pick, uint4* hot,
-                                uint32_t n) {
+__global__ void hot_fill_kernel(const unsigned long long* keys, const uint32_t* rank,
+                                const unsigned long long* pick, uint4* hot, uint32_t n) {
   for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
     const unsigned long long v = pick[h];
     if (!v) continue;
     const uint32_t r = 0xFFFFFFFFu - (uint32_t)v;
     const unsigned long long key = keys[r];
-    hot[h] = make_uint4((uint32_t)key, (uint32_t)(key >> 32), r, (uint32_t)(v >> 32));
+    hot[h] = make_uint4((uint32_t)key, (uint32_t)(key >> 32), rank[r], (uint32_t)(v >> 32));
   }
 }
 
 }  // namespace
 
-void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const PassCtl* ctl, uint4* hot,
-                      unsigned long long* hot_pick, uint32_t hot_log2, cudaStream_t s) {
+void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const uint32_t* rank,
+                      const PassCtl* ctl, uint4* hot, unsigned long long* hot_pick, uint32_t hot_log2,
+                      cudaStream_t s) {
   const uint32_t n = 1u << hot_log2;
   const int g = (int)((n + 255) / 256);
   hot_clear_kernel<<<g, 256, 0, s>>>(hot, hot_pick, n);
   hot_pick_kernel<<<512, 256, 0, s>>>(keys, sel_count, ctl, hot_pick, hot_log2);
-  hot_fill_kernel<<<g, 256, 0, s>>>(keys, hot_pick, hot, n);
+  hot_fill_kernel<<<g, 256, 0, s>>>(keys, rank, hot_pick, hot, n);
 }
 
-void launch_build_candidates(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
-                             bool from_base, uint32_t symbol_bits, unsigned long long* keys_next, uint4* table,
-                             uint32_t table_log2, cudaStream_t s) {
+void launch_build_keys(const uint32_t* sel_slot, const PassCtl* ctl, const unsigned long long* keys_prev,
+                       bool from_base, uint32_t symbol_bits, unsigned long long* keys_next, cudaStream_t s) {
+  keys_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, keys_prev, from_base, symbol_bits, keys_next);
+}
+
+void launch_build_table(const unsigned long long* keys, const uint32_t* rank, const PassCtl* ctl, uint4* table,
+                        uint32_t table_log2, cudaStream_t s) {
   const uint32_t n = 1u << table_log2;
   table_clear_kernel<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, s>>>(table, n);
-  build_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, keys_prev, from_base, symbol_bits, keys_next, table,
-                                    table_log2, const_cast<PassCtl*>(ctl));
+  build_kernel<<<1024, 256, 0, s>>>(keys, rank, ctl, table, table_log2, const_cast<PassCtl*>(ctl));
 }
 
 void launch_write_topk(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
