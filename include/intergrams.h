@@ -58,7 +58,7 @@ typedef enum {
                                       (on the plan's stream) for intergrams_timings */
 
 typedef struct {
-  uint32_t n;            /* target n-gram length in symbols: 1..64 (bytes), 1..32 (2-bit) */
+  uint32_t n;            /* target n-gram length in symbols: 1..64 */
   uint32_t k;            /* number of results wanted, >= 1 */
   uint32_t candidates;   /* Z: size of each intermediate candidate set P^(j); k <= Z < 2^24 */
   uint32_t base_n;       /* length of the dense first pass: 1..3 (bytes), 1..12 (2-bit);
@@ -79,6 +79,12 @@ typedef struct {
   uint32_t table_load_pct;   /* maximum load of the candidate probe table, percent (10..50) */
   uint32_t hot_log2;         /* log2 entries of the shared-memory cache of the most frequent
                                 candidates in front of the probe table (6..13; default 11) */
+  uint32_t chain_from;       /* first pass run from the previous pass's survivor lists instead of a
+                                corpus scan (default: none); passes whose (j-1)-gram exceeds 64 bits
+                                always run this way */
+  uint32_t list_pct;         /* capacity of each survivor list, percent of the corpus symbols
+                                (default: 100 when two full lists fit in 25% of the free device
+                                memory, else 25; exceeding it returns IG_ETABLE_FULL) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -37,7 +37,8 @@ class IgParams(ctypes.Structure):
 
 class IgTuning(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint32) for f in
-                ("ctas_per_sm", "threads", "words_per_thread", "smem_set_log2", "table_load_pct", "hot_log2")]
+                ("ctas_per_sm", "threads", "words_per_thread", "smem_set_log2", "table_load_pct", "hot_log2",
+                 "chain_from", "list_pct")]
 
 
 class IgPassStats(ctypes.Structure):

@@ -77,7 +77,7 @@ struct ig_plan {
   uint32_t table_log2 = 0;
   unsigned long long* keys[2] = {nullptr, nullptr};
   int cur = 0;             // keys[cur] = keys of the latest candidate set
-  uint32_t* sel_slot = nullptr;
+  uint32_t* sel_hist = nullptr;      // selection of every pass j (byte-order slots), Z per pass
   uint32_t* sel_count = nullptr;
   uint32_t* rank = nullptr;          // rank of each candidate id (counter row of the next scan)
   uint32_t* hist = nullptr;
@@ -92,6 +92,16 @@ struct ig_plan {
   uint32_t hot_log2 = 0;
   uint32_t* spill = nullptr;         // Eq. 2: per scan CTA, spill list + partition buffer
   uint64_t spill_cap = 0;
+  // chain mode: per-tile survivor lists, ping-pong by pass parity
+  uint32_t chain_from = 0;           // first pass run from survivor lists
+  uint32_t tile_windows = 0;
+  uint32_t* d_tile_base = nullptr;   // m + 1
+  uint32_t ntiles = 0;
+  uint32_t runs_per_tile = 1;
+  unsigned long long* lists[2] = {nullptr, nullptr};
+  unsigned long long* list_off[2] = {nullptr, nullptr};
+  uint32_t* list_cnt[2] = {nullptr, nullptr};
+  uint64_t list_cap = 0;
   PassCtl* ctl = nullptr;
   PassCtl* h_ctl = nullptr;  // pinned mirror for status reads
   uint32_t* d_order = nullptr;
@@ -136,7 +146,8 @@ void release(ig_plan* pl) {
       if (e) cudaEventDestroy(e);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   void* ptrs[] = {pl->own_data, pl->own_offsets, pl->counts, pl->table, pl->keys[0], pl->keys[1],
-                  pl->sel_slot, pl->sel_count, pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
+                  pl->sel_hist, pl->sel_count, pl->d_tile_base, pl->lists[0], pl->lists[1], pl->list_off[0],
+                  pl->list_off[1], pl->list_cnt[0], pl->list_cnt[1], pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
                   pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank};
   for (void* q : ptrs)
@@ -146,12 +157,28 @@ void release(ig_plan* pl) {
 }
 
 // Enqueue pass j (no host synchronisation).
+// How pass j runs: the dense base pass; a scan of the corpus that probes each
+// window's (j-1)-gram by key (keys of up to 64 bits); or a chain pass driven
+// by the survivor lists of pass j-1 (any key length; work proportional to the
+// survivors). Chain mode is monotone in j.
+enum PassMode : uint32_t { kModeBase = 0, kModeShort = 1, kModeChain = 2, kModeNone = 3 };
+
+uint32_t mode_of(const ig_plan* pl, uint32_t j) {
+  if (j > pl->p.n) return kModeNone;
+  if (j == pl->b) return kModeBase;
+  if (j == pl->b + 1) return kModeShort;
+  if ((j - 1) * pl->sb > 64 || j >= pl->chain_from) return kModeChain;
+  return kModeShort;
+}
+
 // Enqueue pass j (no host synchronisation); returns the kernels launched.
 uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
-  const bool base = (j == pl->b);
+  const uint32_t md = mode_of(pl, j), md_next = mode_of(pl, j + 1);
+  const bool base = (md == kModeBase);
   const bool timing = (pl->p.flags & IG_F_TIMING) != 0;
   const uint32_t ti = j - pl->b;
   const uint64_t ns = base ? pl->nslots_base : pl->nslots_cand;
+  uint32_t* sel = pl->sel_hist + (uint64_t)(j - pl->b) * pl->p.candidates;
   uint32_t kernels = 0;
   // inside a stream capture an event record must be an explicit graph node
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -184,17 +211,33 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.tile_words = pl->tile_words;
   a.queue_words = pl->queue_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
-  // pass j reads the survivors of pass j-1 (written by candidate passes only)
-  // and writes its own when pass j+1 will read them
-  a.alive_in = (j >= pl->b + 2) ? pl->alive[(j - 1) & 1u] : nullptr;
-  a.alive_out = (j >= pl->b + 1 && j + 1 <= pl->p.n) ? pl->alive[j & 1u] : nullptr;
+  a.tile_base = pl->d_tile_base;
+  a.tile_windows = pl->tile_windows;
+  a.runs_per_tile = pl->runs_per_tile;
+  // survivor bitmasks link consecutive scans; survivor lists feed chain passes
+  a.alive_in = (md == kModeShort && j >= pl->b + 2 && mode_of(pl, j - 1) == kModeShort)
+                   ? pl->alive[(j - 1) & 1u] : nullptr;
+  a.alive_out = (md == kModeShort && md_next == kModeShort) ? pl->alive[j & 1u] : nullptr;
   if (a.alive_out) cudaMemsetAsync(a.alive_out, 0, pl->alive_words * sizeof(uint32_t), s);
+  if (md_next == kModeChain) {
+    a.list_out = pl->lists[j & 1u];
+    a.list_out_off = pl->list_off[j & 1u];
+    a.list_out_cnt = pl->list_cnt[j & 1u];
+    a.list_cap = pl->list_cap;
+    cudaMemsetAsync(a.list_out_cnt, 0, (size_t)pl->ntiles * pl->runs_per_tile * sizeof(uint32_t), s);
+  }
+  if (md == kModeChain) {
+    a.list_in = pl->lists[(j - 1) & 1u];
+    a.list_in_off = pl->list_off[(j - 1) & 1u];
+    a.list_in_cnt = pl->list_cnt[(j - 1) & 1u];
+  }
   a.hot = pl->hot;
-  a.hot_log2 = base ? 0u : pl->hot_log2;
+  a.hot_log2 = (md == kModeShort) ? pl->hot_log2 : 0u;
   a.ctl = pl->ctl;
   if (timing) cudaEventRecordWithFlags(pl->ev_scan0[ti], s, evf);
   if (pl->m > 0) {
-    launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
+    if (md == kModeChain) launch_chain(a, pl->sb, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
+    else launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
     kernels += 1;
   }
   if (timing) cudaEventRecordWithFlags(pl->ev_scan1[ti], s, evf);
@@ -202,19 +245,23 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   // the scan of a candidate pass counted in rank space; selection reads the
   // counters back in byte order through the rank map
   launch_select(pl->counts, base ? nullptr : pl->rank, pl->sb, ns, target, pl->ctl, pl->hist, pl->blk, pl->G,
-                pl->sel_slot, pl->sel_count, s);
+                sel, pl->sel_count, s);
   kernels += 12;
   if (j < pl->p.n) {
     const int nxt = pl->cur ^ 1;
-    // P^(j): keys in byte order, then ranks by (count desc, id asc) for the
-    // next scan's counters, then the probe table and hot cache (key -> rank)
-    launch_build_keys(pl->sel_slot, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], s);
+    // P^(j): the next scan's keys (byte-order keys for a key probe, scan
+    // slots for a chain pass), then ranks by (count desc, id asc) for the
+    // next counters, then the probe table (key -> rank) and hot cache
+    if (md_next == kModeShort)
+      launch_build_keys(sel, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], s);
+    else
+      launch_chain_keys(sel, pl->ctl, pl->rank, base, pl->sb, pl->keys[nxt], s);
     launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
                          pl->shist, s);
     launch_rank(pl->sidx[0], pl->ctl, pl->rank, pl->p.candidates, s);
     launch_build_table(pl->keys[nxt], pl->rank, pl->ctl, pl->table, pl->table_log2, s);
     kernels += 1 + 13 + 2 + 2;
-    if (pl->hot_log2) {
+    if (pl->hot_log2 && md_next == kModeShort) {
       launch_build_hot(pl->keys[nxt], pl->sel_count, pl->rank, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
       kernels += 3;
     }
@@ -237,6 +284,7 @@ ig_status read_status(ig_plan* pl) {
   const uint32_t st = pl->h_ctl->status;
   pl->nsel_last = pl->h_ctl->nsel;
   if (st & kStCountOverflow) return fail(IG_EOVERFLOW, "a 32-bit count overflowed");
+  if (st & kStListFull) return fail(IG_ETABLE_FULL, "a survivor list exceeded its capacity (raise list_pct)");
   if (st & (kStSetFull | kStTableFull)) return fail(IG_ETABLE_FULL, "a device hash table filled up");
   if (st) return fail(IG_ECUDA, "device status error");
   return IG_OK;
@@ -255,9 +303,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   *out = nullptr;
   if (!p) return fail(IG_EINVAL, "params is NULL");
   if (p->symbol_bits != 8 && p->symbol_bits != 2) return fail(IG_EINVAL, "symbol_bits must be 8 or 2");
-  const uint32_t max_n = p->symbol_bits == 8 ? 8u : 32u;
-  if (p->n < 1 || p->n > max_n)
-    return fail(IG_EINVAL, "n out of range (this build supports n <= 8 bytes or n <= 32 bases)");
+  if (p->n < 1 || p->n > 64) return fail(IG_EINVAL, "n must be in 1..64");
   if (p->k < 1) return fail(IG_EINVAL, "k must be >= 1");
   if (p->candidates < p->k || p->candidates >= (1u << 24)) return fail(IG_EINVAL, "need k <= candidates < 2^24");
   const uint32_t max_base = p->symbol_bits == 8 ? 3u : 12u;
@@ -333,9 +379,11 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (!t.smem_set_log2) t.smem_set_log2 = 15;
   if (!t.table_load_pct) t.table_load_pct = 25;
   if (!t.hot_log2) t.hot_log2 = 11;
+  const bool auto_list = (t.list_pct == 0);
+  if (!t.list_pct) t.list_pct = 25;
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
-      t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13)
+      t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13 || t.list_pct > 200)
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;
 
@@ -367,9 +415,10 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   pl->tile_words = (pl->tile_words + 3) & ~3u;
   pl->queue_words = (uint32_t)(((tile_windows + 1) / 2 + 3) & ~3ull);
   const uint32_t alive_tile_words = (uint32_t)((tile_windows + 31) / 32);
+  // (+ the results of one run chunk after the survivor bits)
   auto smem_for = [&](uint32_t set_log2) {
     return ((size_t)4 << set_log2) + (size_t)12 * (pl->hot_log2 ? (1u << pl->hot_log2) : 0u) +
-           (size_t)4 * (pl->tile_words + pl->queue_words + alive_tile_words);
+           (size_t)4 * (pl->tile_words + pl->queue_words + ((alive_tile_words + 3) & ~3u) + kRunChunk);
   };
   int max_optin = 0;
   PLAN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
@@ -378,6 +427,9 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   pl->scan_threads = (int)t.threads;
   pl->scan_smem = smem_for(t.smem_set_log2);
   for (bool base : {true, false}) PLAN_CUDA(scan_set_smem_limit(pl->sb, base, pl->scan_smem));
+  PLAN_CUDA(chain_set_smem_limit(pl->sb, pl->scan_smem));
+  pl->tile_windows = (uint32_t)tile_windows;
+  pl->runs_per_tile = (uint32_t)((tile_windows + kRunChunk - 1) / kRunChunk);
   int occ = std::min(scan_max_ctas_per_sm(pl->sb, false, pl->scan_threads, pl->scan_smem),
                      scan_max_ctas_per_sm(pl->sb, true, pl->scan_threads, pl->scan_smem));
   if (occ < 1) return bail(fail(IG_EINVAL, "scan kernel does not fit on an SM with these tuning knobs"));
@@ -386,6 +438,20 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   // Eq. 2 spill buffers: per scan CTA a list and a partition buffer, each
   // holding every window of the longest sequence
   if (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE) pl->spill_cap = std::max<uint64_t>(pl->max_len, 1);
+
+  // chain passes: from pass chain_from on (and whenever a (j-1)-gram key
+  // exceeds 64 bits) a pass runs from the previous pass's survivor lists
+  pl->chain_from = t.chain_from ? t.chain_from : p->n + 1;
+  bool any_chain = false;
+  for (uint32_t j = pl->b; j <= p->n; ++j) any_chain = any_chain || mode_of(pl, j) == kModeChain;
+  std::vector<uint32_t> tile_base((size_t)m + 1, 0);
+  for (uint32_t i = 0; i < m; ++i) {
+    const uint64_t L = pl->h_offsets[i + 1] - pl->h_offsets[i];
+    const uint64_t nt = (L + tile_windows - 1) / tile_windows;
+    if ((uint64_t)tile_base[i] + nt > 0xFFFFFFFFull) return bail(fail(IG_EINVAL, "too many tiles"));
+    tile_base[i + 1] = tile_base[i] + (uint32_t)nt;
+  }
+  pl->ntiles = tile_base[m];
 
   PLAN_CUDA(dev_alloc(&pl->counts, nslots));
   pl->alive_words = (pl->total_syms + 31) / 32 + 1;
@@ -400,7 +466,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   PLAN_CUDA(dev_alloc(&pl->table, (size_t)1 << pl->table_log2));
   PLAN_CUDA(dev_alloc(&pl->keys[0], p->candidates));
   PLAN_CUDA(dev_alloc(&pl->keys[1], p->candidates));
-  PLAN_CUDA(dev_alloc(&pl->sel_slot, p->candidates));
+  PLAN_CUDA(dev_alloc(&pl->sel_hist, (size_t)(p->n - pl->b + 1) * p->candidates));
   PLAN_CUDA(dev_alloc(&pl->sel_count, p->candidates));
   PLAN_CUDA(dev_alloc(&pl->rank, p->candidates));
   PLAN_CUDA(dev_alloc(&pl->hist, (size_t)kMaxLevels * kHistBins));
@@ -411,6 +477,25 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   PLAN_CUDA(dev_alloc(&pl->skey[1], pl->sort_cap));
   PLAN_CUDA(dev_alloc(&pl->shist, (size_t)kSortDigits * sortG));
   if (pl->spill_cap) PLAN_CUDA(dev_alloc(&pl->spill, (size_t)pl->scan_grid * 2 * pl->spill_cap));
+  PLAN_CUDA(dev_alloc(&pl->d_tile_base, (size_t)m + 1));
+  PLAN_CUDA(cudaMemcpyAsync(pl->d_tile_base, tile_base.data(), sizeof(uint32_t) * ((size_t)m + 1),
+                            cudaMemcpyHostToDevice, pl->stream));
+  if (any_chain) {
+    // default capacity: every window when two such lists use at most 25% of the
+    // free device memory, else list_pct (25%) of the windows
+    uint64_t list_pct = t.list_pct;
+    if (auto_list) {
+      size_t free_b = 0, total_b = 0;
+      PLAN_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      if ((long double)2 * 8 * pl->total_syms <= 0.25L * free_b) list_pct = 100;
+    }
+    pl->list_cap = std::max<uint64_t>(1u << 16, pl->total_syms * list_pct / 100);
+    for (int q = 0; q < 2; ++q) {
+      PLAN_CUDA(dev_alloc(&pl->lists[q], pl->list_cap));
+      PLAN_CUDA(dev_alloc(&pl->list_off[q], std::max<size_t>((size_t)pl->ntiles * pl->runs_per_tile, 1)));
+      PLAN_CUDA(dev_alloc(&pl->list_cnt[q], std::max<size_t>((size_t)pl->ntiles * pl->runs_per_tile, 1)));
+    }
+  }
   PLAN_CUDA(dev_alloc(&pl->ctl, 1));
   PLAN_CUDA(cudaMemsetAsync(pl->ctl, 0, sizeof(PassCtl), pl->stream));
   PLAN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&pl->h_ctl), sizeof(PassCtl)));
@@ -515,12 +600,9 @@ ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out, 
   cudaStream_t s = pl->stream;
   launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
                        pl->shist, s);
-  // keys of the selected j-grams: parent keys are P^(j-1) (for j < n the
-  // buffers were flipped after P^(j) was built, so P^(j-1) is keys[cur^1])
-  const bool base = (j == pl->b);
-  const unsigned long long* prev = (j < pl->p.n) ? pl->keys[pl->cur ^ 1] : pl->keys[pl->cur];
+  // symbols of each selected j-gram: walk back through every pass's selection
   const uint32_t rb = row_bytes_for(pl, j);
-  launch_write_topk(pl->sel_slot, pl->sel_count, pl->sidx[0], pl->ctl, prev, base, pl->sb, j, rb, rows,
+  launch_write_topk(pl->sel_hist, pl->p.candidates, pl->b, pl->sel_count, pl->sidx[0], pl->ctl, pl->sb, j, rb, rows,
                     pl->out_keys, pl->out_counts, s);
   pl->kernels += 14;  // sort: init + 4 x (histogram, scan, scatter); write
   IG_CUDA(cudaGetLastError());

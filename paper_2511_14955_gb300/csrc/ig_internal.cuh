@@ -17,6 +17,7 @@ constexpr int kHistBins = 4096;      // bins of one threshold-search level
 constexpr int kMaxLevels = 4;        // threshold-search levels (4096^k >= 2^32 at k = 3; one spare)
 constexpr int kSortDigits = 256;     // 8-bit digits of the final stable sort
 constexpr int kSortChunk = 1024;     // elements per one-warp block of the stable sort
+constexpr uint32_t kRunChunk = 2048; // survivors are listed in runs of at most this many candidates
 
 // Sticky device status bits (PassCtl::status).
 enum : uint32_t {
@@ -24,6 +25,7 @@ enum : uint32_t {
   kStTableFull = 1u << 1,      // the candidate probe table had no empty slot
   kStCountOverflow = 1u << 2,  // a 32-bit count wrapped (Eq. 1 only)
   kStQueue = 1u << 3,          // work queue inconsistency
+  kStListFull = 1u << 4,       // a survivor list ran out of its capacity
 };
 
 // Device-side control block, one per plan. The pass fields are zeroed at the
@@ -49,6 +51,7 @@ struct PassCtl {
   uint32_t epoch_next;
   uint32_t gset_clear;               // epochs wrapped: clear the dedupe sets before the scan
   uint32_t pad;
+  unsigned long long list_used;      // entries reserved in this pass's survivor list
 };
 
 struct ScanArgs {
@@ -79,14 +82,30 @@ struct ScanArgs {
   // shared-memory cache of the most frequent candidates {key lo, key hi, id, count}
   const uint4* hot;
   uint32_t hot_log2;           // 0 = no cache
+  // survivor lists (chain mode): tile g (tile_base[seq] + window / tile windows)
+  // has runs_per_tile runs of entries (slot << 32 | window index in the
+  // sequence); run r of tile g is at off[g * runs + r], cnt[g * runs + r] entries
+  const uint32_t* tile_base;   // m + 1 entries
+  uint32_t tile_windows;
+  const unsigned long long* list_in;       // previous pass's list (chain passes)
+  const unsigned long long* list_in_off;
+  const uint32_t* list_in_cnt;
+  unsigned long long* list_out;            // this pass's list (null = not written)
+  unsigned long long* list_out_off;
+  uint32_t* list_out_cnt;
+  unsigned long long list_cap;
+  uint32_t runs_per_tile;
   PassCtl* ctl;
 };
 
 // Launchers (ig_scan.cu)
 void launch_scan(const ScanArgs& a, uint32_t symbol_bits, bool base_pass, int grid, int threads,
                  size_t smem, cudaStream_t s);
+// candidate pass driven by the previous pass's survivor lists
+void launch_chain(const ScanArgs& a, uint32_t symbol_bits, int grid, int threads, size_t smem, cudaStream_t s);
 int scan_max_ctas_per_sm(uint32_t symbol_bits, bool base_pass, int threads, size_t smem);
 cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem);
+cudaError_t chain_set_smem_limit(uint32_t symbol_bits, size_t smem);
 // Raise (never lower) the scan kernel's dynamic shared-memory limit to `smem`.
 cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem);
 
@@ -113,10 +132,15 @@ void launch_build_table(const unsigned long long* keys, const uint32_t* rank, co
 void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const uint32_t* rank,
                       const PassCtl* ctl, uint4* hot, unsigned long long* hot_pick, uint32_t hot_log2,
                       cudaStream_t s);
-void launch_write_topk(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
-                       const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
-                       uint32_t symbol_bits, uint32_t j, uint32_t row_bytes, uint32_t cap,
-                       uint8_t* keys_out, unsigned long long* counts_out, cudaStream_t s);
+// rows of the top-k of pass j: symbols rebuilt by walking back through every
+// pass's selection (sel_hist[(jj - b) * Z + id] = byte-order slot of P^(jj))
+void launch_write_topk(const uint32_t* sel_hist, uint64_t Z, uint32_t b, const uint32_t* sel_count,
+                       const uint32_t* order, const PassCtl* ctl, uint32_t symbol_bits, uint32_t j,
+                       uint32_t row_bytes, uint32_t cap, uint8_t* keys_out, unsigned long long* counts_out,
+                       cudaStream_t s);
+// chain keys of P^(j): the scan slot of each selected j-gram (rank space of pass j)
+void launch_chain_keys(const uint32_t* sel_slot, const PassCtl* ctl, const uint32_t* rank_prev, bool from_base,
+                       uint32_t symbol_bits, unsigned long long* keys_out, cudaStream_t s);
 
 // ------------------------------------------------------------- helpers
 

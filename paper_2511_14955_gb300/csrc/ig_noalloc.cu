@@ -165,9 +165,9 @@ extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void
                        reinterpret_cast<uint32_t*>(S + L.idx0), reinterpret_cast<uint32_t*>(S + L.idx1),
                        reinterpret_cast<uint32_t*>(S + L.key0), reinterpret_cast<uint32_t*>(S + L.key1),
                        reinterpret_cast<uint32_t*>(S + L.shist), s);
-  launch_write_topk(reinterpret_cast<uint32_t*>(S + L.sel_slot), reinterpret_cast<uint32_t*>(S + L.sel_count),
-                    reinterpret_cast<uint32_t*>(S + L.idx0), ctl, nullptr, true, sb, n, (n * sb + 7) / 8, p->k,
-                    keys_out, reinterpret_cast<unsigned long long*>(counts_out), s);
+  launch_write_topk(reinterpret_cast<uint32_t*>(S + L.sel_slot), 0, n, reinterpret_cast<uint32_t*>(S + L.sel_count),
+                    reinterpret_cast<uint32_t*>(S + L.idx0), ctl, sb, n, (n * sb + 7) / 8, p->k, keys_out,
+                    reinterpret_cast<unsigned long long*>(counts_out), s);
   rows_kernel<<<1, 32, 0, s>>>(ctl, p->k, rows_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bad(IG_ECUDA, cudaGetErrorString(e));

@@ -105,6 +105,14 @@ __device__ __forceinline__ uint64_t tile_key(const uint32_t* tile, uint32_t o, u
   return bits >= 64 ? v : (v >> (64 - bits));
 }
 
+// Symbol `o` of the tile.
+template <int SB>
+__device__ __forceinline__ uint32_t tile_sym(const uint32_t* tile, uint32_t o) {
+  const uint32_t bit = o * SB;
+  const uint32_t w = __byte_perm(tile[bit >> 5], 0, 0x0123);
+  return (w >> (32 - SB - (bit & 31))) & ((1u << SB) - 1u);
+}
+
 // Phase 1 of the spill dedupe: bounded probe of the shared-memory set of the
 // current sequence. 0 = already present, 1 = inserted (first occurrence),
 // 2 = no room on the probe path (the slot goes to the spill list). A slot that
@@ -250,7 +258,8 @@ __device__ void dedupe_spills(const ScanArgs& a, uint32_t S, uint32_t* sset, uin
 template <int SB, bool BASE>
 __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_item, s_nspill, s_qn;
+  __shared__ uint32_t s_item, s_nspill, s_qn, s_lcnt, s_ccnt;
+  __shared__ unsigned long long s_lbase;
   __shared__ unsigned long long s_surv, s_regs;
 
   using S = Sym<SB>;
@@ -269,6 +278,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   uint16_t* queue = reinterpret_cast<uint16_t*>(tile + a.tile_words);
   uint32_t* tile_alive = tile + a.tile_words + a.queue_words;
   const uint32_t alive_tile_words = (tile_windows + 31) / 32;
+  uint32_t* res = tile_alive + ((alive_tile_words + 3) & ~3u);   // kRunChunk results of a chunk
   unsigned long long* gset = a.gset ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
   // CTA-private spill list and partition buffer (Eq. 2 without a global set)
   uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
@@ -415,36 +425,72 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           if (tid == 0) s_qn = nwin;
         }
         __syncthreads();
-        // phase B: probe, count, dedupe the queued windows
+        // phase B: probe, count, dedupe the queued windows, in chunks of
+        // kRunChunk; a chunk's survivors form one run of the survivor list
         const uint32_t qn = s_qn;
-        for (uint32_t qi = tid; qi < qn; qi += nthr) {
-          const uint32_t w = queue[qi];
-          const uint64_t key = tile_key<SB>(tile, sym_off + w, j);
-          const uint64_t prefix = key >> SB;
-          uint32_t id = kEmpty32;
-          if (H) {
-            const uint32_t h = hash64_top(prefix, a.hot_log2);
-            if (hot_keys[h] == prefix) id = hot_ids[h];
-          }
-          if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
-          if (id == kEmpty32) continue;
-          const uint32_t slot = (id << SB) | (uint32_t)(key & S::kMask);
-          if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
-          ++my_surv;
-          bool count_it = true;
-          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-            if (spill_list) {
-              const int r = sset_try_insert(sset, slog, slot);
-              count_it = (r == 1);
-              if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
-            } else {
-              count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
+        const uint32_t tile_g = a.tile_base[seq] + (uint32_t)(w0 / a.tile_windows);
+        // without a list to write the whole queue is one chunk (no extra barriers)
+        const uint32_t chunk = a.list_out ? kRunChunk : (qn ? qn : 1u);
+        for (uint32_t c0 = 0; c0 < qn; c0 += chunk) {
+          const uint32_t ce = (qn - c0) < chunk ? qn : c0 + chunk;
+          if (tid == 0) s_ccnt = 0;
+          __syncthreads();
+          for (uint32_t qi = c0 + tid; qi < ce; qi += nthr) {
+            const uint32_t w = queue[qi];
+            const uint64_t prefix = tile_key<SB>(tile, sym_off + w, j - 1);
+            const uint32_t last = tile_sym<SB>(tile, sym_off + w + j - 1);
+            uint32_t id = kEmpty32;
+            if (H) {
+              const uint32_t h = hash64_top(prefix, a.hot_log2);
+              if (hot_keys[h] == prefix) id = hot_ids[h];
+            }
+            if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
+            if (a.list_out) res[qi - c0] = id == kEmpty32 ? kEmpty32 : ((id << SB) | last);
+            if (id == kEmpty32) continue;
+            const uint32_t slot = (id << SB) | last;
+            if (a.list_out) atomicAdd(&s_ccnt, 1u);
+            if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
+            ++my_surv;
+            bool count_it = true;
+            if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+              if (spill_list) {
+                const int r = sset_try_insert(sset, slog, slot);
+                count_it = (r == 1);
+                if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+              } else {
+                count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
+              }
+            }
+            if (count_it) {
+              ++my_regs;
+              register_slot(a, slot);
             }
           }
-          if (count_it) {
-            ++my_regs;
-            register_slot(a, slot);
+          if (a.list_out) {
+            __syncthreads();
+            if (tid == 0) {
+              unsigned long long base = atomicAdd(&a.ctl->list_used, (unsigned long long)s_ccnt);
+              if (base + s_ccnt > a.list_cap) {
+                atomicOr(&a.ctl->status, kStListFull);
+                base = ~0ull;
+              }
+              s_lbase = base;
+              s_lcnt = 0;
+              const uint32_t run = tile_g * a.runs_per_tile + c0 / kRunChunk;
+              a.list_out_off[run] = base;
+              a.list_out_cnt[run] = base == ~0ull ? 0u : s_ccnt;
+            }
+            __syncthreads();
+            if (s_lbase != ~0ull) {
+              for (uint32_t qi = c0 + tid; qi < ce; qi += nthr) {
+                const uint32_t slot = res[qi - c0];
+                if (slot != kEmpty32)
+                  a.list_out[s_lbase + atomicAdd(&s_lcnt, 1u)] =
+                      ((unsigned long long)slot << 32) | (uint32_t)(w0 + queue[qi]);
+              }
+            }
           }
+          __syncthreads();
         }
         if (a.alive_out) {
           __syncthreads();
@@ -484,6 +530,136 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   }
 }
 
+
+// Candidate pass j driven by survivor lists. An entry of pass j-1 says that
+// window w of the sequence survived pass j-1 with scan slot s; the window's
+// (j-1)-gram is in P^(j-1) exactly when s was selected, which the probe table
+// (keyed by slot) answers with the counter row of pass j. The last symbol is
+// read from the corpus. No tile is staged: work is proportional to the
+// survivors of pass j-1, and keys of any length stay exact.
+template <int SB>
+__global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_item, s_nspill, s_lcnt, s_ccnt;
+  __shared__ unsigned long long s_lbase, s_surv, s_regs;
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+  uint32_t* sset = smem;
+  uint32_t* scratch = smem + (1u << a.sset_log2);
+  uint32_t* res = scratch;  // kRunChunk results of the current run (free during the spill dedupe)
+  uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
+  uint32_t* spill_part = spill_list ? spill_list + a.spill_cap : nullptr;
+  const uint32_t j = a.j, T = a.tile_windows;
+  unsigned long long my_surv = 0, my_regs = 0;
+  if (tid == 0) { s_surv = 0; s_regs = 0; }
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(&a.ctl->queue, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= a.m) break;
+    const uint32_t seq = a.order[item];
+    const uint64_t s0 = a.offsets[seq];
+    const uint64_t L = a.offsets[seq + 1] - s0;
+    if (L < j) continue;
+    const uint64_t W = L - j + 1;
+    uint32_t slog = 0;
+    if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+      const uint32_t need = ceil_log2_u64(2 * W);
+      slog = need < a.sset_log2 ? need : a.sset_log2;
+      if (slog < 1) slog = 1;
+      for (uint32_t i = tid; i < (1u << slog); i += nthr) sset[i] = kEmpty32;
+    }
+    if (tid == 0) s_nspill = 0;
+    const uint32_t g0 = a.tile_base[seq];
+    const uint32_t ntiles = (uint32_t)((W + 1 + T - 1) / T);   // tiles of pass j-1 (W + 1 windows)
+    __syncthreads();
+    for (uint32_t t = 0; t < ntiles; ++t) {
+      for (uint32_t r = 0; r < a.runs_per_tile; ++r) {
+        const uint32_t run = (g0 + t) * a.runs_per_tile + r;
+        const uint32_t n_in = a.list_in_cnt[run];
+        if (n_in == 0) continue;  // uniform across the CTA
+        const unsigned long long off_in = a.list_in_off[run];
+        if (tid == 0) s_ccnt = 0;
+        __syncthreads();
+        for (uint32_t e = tid; e < n_in; e += nthr) {
+          const unsigned long long ent = a.list_in[off_in + e];
+          const uint32_t w = (uint32_t)ent;
+          res[e] = kEmpty32;
+          if (w >= W) continue;  // the last window of pass j-1 has no j-gram
+          const uint64_t pos = s0 + w + j - 1;
+          uint32_t sym;
+          if (SB == 8) {
+            sym = __ldg(a.data + pos);
+          } else {
+            sym = (__ldg(a.data + (pos >> 2)) >> (6 - 2 * (pos & 3))) & 3u;
+          }
+          const uint32_t id = probe_table(a.table, a.table_log2, ent >> 32, a.ctl);
+          if (id == kEmpty32) continue;
+          const uint32_t slot = (id << SB) | sym;
+          res[e] = slot;
+          atomicAdd(&s_ccnt, 1u);
+          ++my_surv;
+          bool count_it = true;
+          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+            const int rr = sset_try_insert(sset, slog, slot);
+            count_it = (rr == 1);
+            if (rr == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+          }
+          if (count_it) {
+            ++my_regs;
+            register_slot(a, slot);
+          }
+        }
+        if (a.list_out) {
+          // this run's survivors form run r of tile g in the next list
+          __syncthreads();
+          if (tid == 0) {
+            unsigned long long base = atomicAdd(&a.ctl->list_used, (unsigned long long)s_ccnt);
+            if (base + s_ccnt > a.list_cap) {
+              atomicOr(&a.ctl->status, kStListFull);
+              base = ~0ull;
+            }
+            s_lbase = base;
+            s_lcnt = 0;
+            a.list_out_off[run] = base;
+            a.list_out_cnt[run] = base == ~0ull ? 0u : s_ccnt;
+          }
+          __syncthreads();
+          if (s_lbase != ~0ull) {
+            for (uint32_t e = tid; e < n_in; e += nthr) {
+              const uint32_t slot = res[e];
+              if (slot != kEmpty32)
+                a.list_out[s_lbase + atomicAdd(&s_lcnt, 1u)] =
+                    ((unsigned long long)slot << 32) | (uint32_t)a.list_in[off_in + e];
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+      __syncthreads();
+      const uint32_t nsp = s_nspill;
+      if (nsp) dedupe_spills(a, nsp, sset, scratch, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    my_surv += __shfl_down_sync(0xffffffffu, my_surv, o);
+    my_regs += __shfl_down_sync(0xffffffffu, my_regs, o);
+  }
+  if ((tid & 31) == 0) {
+    atomicAdd(&s_surv, my_surv);
+    atomicAdd(&s_regs, my_regs);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&a.ctl->survivors, s_surv);
+    atomicAdd(&a.ctl->registrations, s_regs);
+  }
+}
+
 template <int SB, bool BASE>
 void* kernel_ptr() {
   return reinterpret_cast<void*>(scan_kernel<SB, BASE>);
@@ -499,6 +675,16 @@ void* pick(uint32_t symbol_bits, bool base_pass) {
 cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem) {
   return cudaFuncSetAttribute(pick(symbol_bits, base_pass), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
+}
+
+cudaError_t chain_set_smem_limit(uint32_t symbol_bits, size_t smem) {
+  void* f = symbol_bits == 8 ? reinterpret_cast<void*>(chain_kernel<8>) : reinterpret_cast<void*>(chain_kernel<2>);
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+void launch_chain(const ScanArgs& a, uint32_t symbol_bits, int grid, int threads, size_t smem, cudaStream_t s) {
+  if (symbol_bits == 8) chain_kernel<8><<<grid, threads, smem, s>>>(a);
+  else chain_kernel<2><<<grid, threads, smem, s>>>(a);
 }
 
 cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem) {

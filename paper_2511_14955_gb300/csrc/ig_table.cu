@@ -59,19 +59,44 @@ __global__ void build_kernel(const unsigned long long* keys, const uint32_t* ran
   }
 }
 
-__global__ void write_topk_kernel(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
-                                  const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
-                                  uint32_t sb, uint32_t j, uint32_t row_bytes, uint32_t cap, uint8_t* keys_out,
+// Row r of the top-k of pass j. The selection of every pass is kept in byte
+// order (sel_hist), and slot = id * sigma + last symbol with id the parent's
+// position in the previous selection, so the j symbols are recovered by
+// walking back to the dense base pass, whose slot is the base_n-gram itself.
+__global__ void write_topk_kernel(const uint32_t* sel_hist, uint64_t Z, uint32_t b, const uint32_t* sel_count,
+                                  const uint32_t* order, const PassCtl* ctl, uint32_t sb, uint32_t j,
+                                  uint32_t row_bytes, uint32_t cap, uint8_t* keys_out,
                                   unsigned long long* counts_out) {
   const uint32_t n = min(ctl->nsel, cap);
+  const uint32_t mask = (1u << sb) - 1u;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const uint32_t e = order[r];
-    const uint32_t slot = sel_slot[e];
     counts_out[r] = sel_count[e];
-    const unsigned long long key = key_of_slot(slot, keys_prev, from_base, sb);
-    const uint32_t bits = j * sb;
-    const unsigned long long v = bits >= 64 ? key : key << (64 - bits);   // left-aligned
-    for (uint32_t b = 0; b < row_bytes; ++b) keys_out[(size_t)r * row_bytes + b] = (uint8_t)(v >> (56 - 8 * b));
+    uint8_t* row = keys_out + (size_t)r * row_bytes;
+    for (uint32_t x = 0; x < row_bytes; ++x) row[x] = 0;
+    uint32_t slot = sel_hist[(uint64_t)(j - b) * Z + e];
+    for (uint32_t jj = j; jj > b; --jj) {
+      const uint32_t p = jj - 1, sym = slot & mask;   // symbol position p (0-based)
+      if (sb == 8) row[p] = (uint8_t)sym;
+      else row[p >> 2] |= (uint8_t)(sym << (6 - 2 * (p & 3)));
+      slot = sel_hist[(uint64_t)(jj - 1 - b) * Z + (slot >> sb)];
+    }
+    for (uint32_t p = 0; p < b; ++p) {
+      const uint32_t sym = (slot >> (sb * (b - 1 - p))) & mask;
+      if (sb == 8) row[p] = (uint8_t)sym;
+      else row[p >> 2] |= (uint8_t)(sym << (6 - 2 * (p & 3)));
+    }
+  }
+}
+
+// Chain keys of P^(j): the scan slot (rank space of pass j) of each selected
+// j-gram, i.e. what pass j wrote into its survivor lists.
+__global__ void chain_keys_kernel(const uint32_t* sel_slot, const PassCtl* ctl, const uint32_t* rank_prev,
+                                  bool from_base, uint32_t sb, unsigned long long* keys_out) {
+  const uint32_t n = ctl->nsel;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const uint32_t s = sel_slot[r];
+    keys_out[r] = from_base ? s : (((uint64_t)rank_prev[s >> sb] << sb) | (s & ((1u << sb) - 1u)));
   }
 }
 
@@ -130,12 +155,17 @@ void launch_build_table(const unsigned long long* keys, const uint32_t* rank, co
   build_kernel<<<1024, 256, 0, s>>>(keys, rank, ctl, table, table_log2, const_cast<PassCtl*>(ctl));
 }
 
-void launch_write_topk(const uint32_t* sel_slot, const uint32_t* sel_count, const uint32_t* order,
-                       const PassCtl* ctl, const unsigned long long* keys_prev, bool from_base,
-                       uint32_t symbol_bits, uint32_t j, uint32_t row_bytes, uint32_t cap, uint8_t* keys_out,
-                       unsigned long long* counts_out, cudaStream_t s) {
-  write_topk_kernel<<<256, 256, 0, s>>>(sel_slot, sel_count, order, ctl, keys_prev, from_base, symbol_bits, j,
-                                        row_bytes, cap, keys_out, counts_out);
+void launch_write_topk(const uint32_t* sel_hist, uint64_t Z, uint32_t b, const uint32_t* sel_count,
+                       const uint32_t* order, const PassCtl* ctl, uint32_t symbol_bits, uint32_t j,
+                       uint32_t row_bytes, uint32_t cap, uint8_t* keys_out, unsigned long long* counts_out,
+                       cudaStream_t s) {
+  write_topk_kernel<<<256, 256, 0, s>>>(sel_hist, Z, b, sel_count, order, ctl, symbol_bits, j, row_bytes, cap,
+                                        keys_out, counts_out);
+}
+
+void launch_chain_keys(const uint32_t* sel_slot, const PassCtl* ctl, const uint32_t* rank_prev, bool from_base,
+                       uint32_t symbol_bits, unsigned long long* keys_out, cudaStream_t s) {
+  chain_keys_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, rank_prev, from_base, symbol_bits, keys_out);
 }
 
 }  // namespace ig

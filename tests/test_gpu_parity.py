@@ -93,6 +93,56 @@ def test_results_do_not_depend_on_tuning(tuning):
     check_all_passes(data, off, n=5, k=700, Z=3000, base_n=2, tuning=tuning)
 
 
+def check_passes(data, off, *, n, k, Z, base_n, js, mode=0, symbol_bits=8, tuning=None):
+    """Run every pass; compare with the oracle after the passes in `js`."""
+    d, o = dev(data, off)
+    pl = B.Plan(d, o, n=n, k=k, candidates=Z, base_n=base_n, symbol_bits=symbol_bits, count_mode=mode,
+                tuning=tuning)
+    while True:
+        j = pl.step()
+        if j is None:
+            break
+        if j in js:
+            gk, gc, gj = pl.topk()
+            ek, ec = O.intergrams(data, off, n, k, Z, base_n=base_n, count_mode=mode, symbol_bits=symbol_bits,
+                                  stop_j=j)
+            ek = oracle_rows(ek, symbol_bits)
+            assert gk.shape == ek.shape, (j, gk.shape, ek.shape)
+            assert np.array_equal(gc, ec), f"counts differ at pass {j}"
+            assert np.array_equal(gk, ek), f"keys differ at pass {j}"
+    pl.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_long_byte_keys(mode):
+    """n = 16 and n = 64 bytes: passes whose (j-1)-gram exceeds 64 bits run from survivor lists."""
+    data, off, _ = synth.make_corpus("largen_6gb", m=24, max_len=12000, seed=4)
+    check_passes(data, off, n=16, k=200, Z=800, base_n=3, js={3, 8, 9, 10, 11, 16}, mode=mode)
+    check_passes(data, off, n=64, k=150, Z=600, base_n=2, js={9, 10, 33, 64}, mode=mode)
+
+
+def test_long_dna_keys():
+    data, off, _ = synth.make_corpus("genomic_5gbp", m=3, max_len=20011, seed=6)
+    check_passes(data, off, n=48, k=100, Z=400, base_n=10, js={32, 33, 34, 35, 48}, symbol_bits=2)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chain_mode_with_short_keys(mode):
+    """Chain passes from pass base+2 on (short keys), against every pass of the oracle."""
+    data, off, _ = synth.make_corpus("malware_8gb", m=30, max_len=40000, seed=8)
+    check_all_passes(data, off, n=8, k=300, Z=1200, base_n=2, mode=mode, tuning=dict(chain_from=4))
+
+
+def test_list_capacity_exceeded_is_reported():
+    data, off, _ = synth.make_corpus("markov_2mb", m=10, seed=3)
+    d, o = dev(data, off)
+    pl = B.Plan(d, o, n=6, k=10, candidates=4000, base_n=1, tuning=dict(chain_from=3, list_pct=1))
+    with pytest.raises(B.IntergramsError) as ei:
+        pl.run()
+    assert ei.value.status == -3
+    pl.close()
+
+
 def test_edge_cases():
     rng = np.random.default_rng(0)
     cases = [
