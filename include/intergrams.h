@@ -56,6 +56,12 @@ typedef enum {
 #define IG_F_AUTOTUNE   (1u << 2)  /* let the autotuner pick the tuning knobs left at 0 */
 #define IG_F_TIMING     (1u << 3)  /* record CUDA events around every scan kernel and pass
                                       (on the plan's stream) for intergrams_timings */
+#define IG_F_OFFSETS_HOST (1u << 4) /* offsets is a HOST pointer (data stays on the device);
+                                       the plan copies the offsets and needs no device read-back */
+#define IG_F_ASYNC_ALLOC (1u << 5) /* allocate and free the plan's tables stream-ordered
+                                      (cudaMallocAsync / cudaFreeAsync on the plan's stream) */
+#define IG_F_DRY_RUN    (1u << 6)  /* size the plan without allocating or launching anything;
+                                      only intergrams_plan_device_bytes and intergrams_free apply */
 
 typedef struct {
   uint32_t n;            /* target n-gram length in symbols: 1..64 */
@@ -152,6 +158,9 @@ ig_status intergrams_rewind(ig_plan* pl);
 ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out,
                           uint32_t capacity, uint32_t* k_out, uint32_t* j_out);
 
+/* Device bytes the plan allocated (or would allocate, for a plan made with IG_F_DRY_RUN). */
+ig_status intergrams_plan_device_bytes(const ig_plan* pl, uint64_t* bytes);
+
 /* Per-pass statistics of the latest pass (device counters, read on demand). */
 typedef struct {
   uint32_t j;               /* n-gram length of the pass */
@@ -212,6 +221,49 @@ ig_status intergrams_timings(ig_plan* pl, float* scan_ms, float* pass_ms, uint32
 ig_status intergrams_dense_topk_static(const ig_params* p, const void* data, const uint64_t* offsets,
                                        uint32_t m, uint64_t total_symbols, void* stream,
                                        uint8_t* keys_out, uint64_t* counts_out, uint32_t* rows_out);
+
+/* ------------------------------------------------------------------ serving
+ * A server runs many top-k jobs on one GPU with continuous batching: a
+ * scheduler thread admits submitted jobs in arrival order whenever a slot is
+ * free and the job's tables fit the device-memory budget, keeps each admitted
+ * job's plan (its candidate and count tables) resident on its own stream, and
+ * advances every active job one pass at a time, so jobs at different passes
+ * have work on the GPU together. A job's result is the same as when it runs
+ * alone (each job owns its tables; kernels are deterministic). max_active = 1
+ * gives one job per launch, in order. No counterpart in the paper, which runs
+ * one job at a time. */
+typedef struct ig_server ig_server;
+typedef struct {
+  uint64_t mem_budget;   /* device bytes all active jobs' tables may use (0 = 80% of free memory) */
+  uint32_t max_active;   /* jobs in flight at once (0 = 8) */
+  uint32_t flags;        /* reserved, 0 */
+} ig_server_config;
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint32_t active, peak_active, pending;
+  uint64_t mem_used, peak_mem, mem_budget;
+} ig_server_stats;
+
+/* Start a server on the current device (its scheduler thread uses that device). */
+ig_status intergrams_server_create(const ig_server_config* cfg, ig_server** out);
+
+/* Queue a job. data: DEVICE corpus (caller-owned, valid until the job is
+ * waited for); offsets: HOST uint64[m + 1] (copied). The job's device bytes
+ * are sized at once (a dry-run plan); IG_ENOMEM if they exceed the budget. */
+ig_status intergrams_server_submit(ig_server* sv, const ig_params* p, const void* data, const uint64_t* offsets,
+                                   uint32_t m, const ig_tuning* tuning, uint64_t* job_id);
+
+/* Wait for a job (timeout_us < 0: no limit; IG_ETIMEOUT when it expires),
+ * copy its top-k (format of intergrams_topk after the last pass) into HOST
+ * buffers and release it. latency_s: submit-to-completion time. Returns the
+ * job's status. */
+ig_status intergrams_server_wait(ig_server* sv, uint64_t job_id, int64_t timeout_us, uint8_t* keys_out,
+                                 uint64_t* counts_out, uint32_t capacity, uint32_t* k_out, double* latency_s);
+
+ig_status intergrams_server_stats(ig_server* sv, ig_server_stats* out);
+
+/* Finish every queued job, stop the scheduler and free the server. */
+void intergrams_server_destroy(ig_server* sv);
 
 /* Release every resource of the plan (stream-ordered frees). NULL is ignored. */
 void intergrams_free(ig_plan* pl);

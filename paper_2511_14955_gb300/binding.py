@@ -27,7 +27,9 @@ F_TIMING = 1 << 3
 # every symbol include/intergrams.h declares
 EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_rewind", "intergrams_topk",
            "intergrams_stats", "intergrams_timings", "intergrams_free", "intergrams_last_error",
-           "intergrams_dense_topk_static"]
+           "intergrams_dense_topk_static", "intergrams_plan_device_bytes", "intergrams_server_create",
+           "intergrams_server_submit", "intergrams_server_wait", "intergrams_server_stats",
+           "intergrams_server_destroy"]
 
 
 class IgParams(ctypes.Structure):
@@ -45,6 +47,16 @@ class IgPassStats(ctypes.Structure):
     _fields_ = [("j", ctypes.c_uint32), ("windows", ctypes.c_uint64), ("survivors", ctypes.c_uint64),
                 ("registrations", ctypes.c_uint64), ("nonzero_selected", ctypes.c_uint64),
                 ("scanned_bytes", ctypes.c_uint64)]
+
+
+class IgServerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_active", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class IgServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("active", ctypes.c_uint32), ("peak_active", ctypes.c_uint32), ("pending", ctypes.c_uint32),
+                ("mem_used", ctypes.c_uint64), ("peak_mem", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64)]
 
 
 class IntergramsError(RuntimeError):
@@ -91,6 +103,20 @@ def load(build_if_missing: bool = True):
     lib.intergrams_free.argtypes = [P]
     lib.intergrams_dense_topk_static.restype = ctypes.c_int
     lib.intergrams_dense_topk_static.argtypes = [ctypes.POINTER(IgParams), P, P, U32, ctypes.c_uint64, P, P, P, P]
+    lib.intergrams_plan_device_bytes.restype = ctypes.c_int
+    lib.intergrams_plan_device_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.intergrams_server_create.restype = ctypes.c_int
+    lib.intergrams_server_create.argtypes = [ctypes.POINTER(IgServerConfig), ctypes.POINTER(ctypes.c_void_p)]
+    lib.intergrams_server_submit.restype = ctypes.c_int
+    lib.intergrams_server_submit.argtypes = [P, ctypes.POINTER(IgParams), P, P, U32, ctypes.POINTER(IgTuning),
+                                             ctypes.POINTER(ctypes.c_uint64)]
+    lib.intergrams_server_wait.restype = ctypes.c_int
+    lib.intergrams_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int64, P, P, U32, ctypes.POINTER(U32),
+                                           ctypes.POINTER(ctypes.c_double)]
+    lib.intergrams_server_stats.restype = ctypes.c_int
+    lib.intergrams_server_stats.argtypes = [P, ctypes.POINTER(IgServerStats)]
+    lib.intergrams_server_destroy.restype = None
+    lib.intergrams_server_destroy.argtypes = [P]
     lib.intergrams_last_error.restype = ctypes.c_char_p
     lib.intergrams_last_error.argtypes = []
     _lib = lib
@@ -234,3 +260,61 @@ def dense_topk_static(data, offsets, *, n: int, k: int, symbol_bits: int = 8,
     st = lib.intergrams_dense_topk_static(ctypes.byref(params), _ptr(data), _ptr(offsets), m, int(total_symbols),
                                           stream_ptr, _ptr(keys_out), _ptr(counts_out), _ptr(rows_out))
     _check(lib, st, "intergrams_dense_topk_static")
+
+
+class Server:
+    """Continuous-batching job server (intergrams_server_*): submit jobs whose
+    corpora are CUDA tensors, wait for their top-k. Marshalling only."""
+
+    def __init__(self, mem_budget: int = 0, max_active: int = 8):
+        self._lib = load()
+        self._h = ctypes.c_void_p(None)
+        cfg = IgServerConfig(int(mem_budget), int(max_active), 0)
+        _check(self._lib, self._lib.intergrams_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
+               "intergrams_server_create")
+        self._keep = {}
+        self._meta = {}
+
+    def submit(self, data, offsets, *, n: int, k: int, candidates: int, base_n: int = 3, symbol_bits: int = 8,
+               count_mode: int = COUNT_ONCE_PER_SEQUENCE, tuning: dict | None = None) -> int:
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        params = IgParams(n, k, candidates, base_n, symbol_bits, count_mode, 0)
+        tun = IgTuning(**(tuning or {}))
+        jid = ctypes.c_uint64(0)
+        _check(self._lib, self._lib.intergrams_server_submit(self._h, ctypes.byref(params), _ptr(data),
+                                                             off.ctypes.data, len(off) - 1, ctypes.byref(tun),
+                                                             ctypes.byref(jid)), "intergrams_server_submit")
+        self._keep[jid.value] = data
+        self._meta[jid.value] = (n, k, symbol_bits)
+        return jid.value
+
+    def wait(self, job_id: int, timeout_s: float | None = None):
+        """(keys, counts, latency_s) of a finished job."""
+        n, k, bits = self._meta.pop(job_id)
+        row = (n * bits + 7) // 8
+        keys = np.zeros((max(k, 1), row), np.uint8)
+        counts = np.zeros(max(k, 1), np.uint64)
+        kout, lat = ctypes.c_uint32(0), ctypes.c_double(0.0)
+        tmo = -1 if timeout_s is None else int(timeout_s * 1e6)
+        st = self._lib.intergrams_server_wait(self._h, job_id, tmo, keys.ctypes.data, counts.ctypes.data, k,
+                                              ctypes.byref(kout), ctypes.byref(lat))
+        self._keep.pop(job_id, None)
+        _check(self._lib, st, "intergrams_server_wait")
+        r = kout.value
+        return keys[:r].copy(), counts[:r].copy(), lat.value
+
+    def stats(self) -> dict:
+        s = IgServerStats()
+        _check(self._lib, self._lib.intergrams_server_stats(self._h, ctypes.byref(s)), "intergrams_server_stats")
+        return {f: getattr(s, f) for f, _ in IgServerStats._fields_}
+
+    def close(self):
+        if self._h and self._h.value:
+            self._lib.intergrams_server_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -35,13 +35,6 @@ ig_status fail(ig_status st, const std::string& msg) {
     }                                                                                          \
   } while (0)
 
-template <class T>
-cudaError_t dev_alloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
-}
-
 }  // namespace
 
 namespace ig {
@@ -120,12 +113,27 @@ struct ig_plan {
   std::vector<cudaEvent_t> ev_pass0, ev_pass1, ev_scan0, ev_scan1;
   uint32_t kernels = 0;              // kernels launched since the last rewind
   uint32_t graph_kernels = 0;        // kernels in the captured graph
+  uint64_t dev_bytes = 0;            // device bytes allocated (or that would be, with IG_F_DRY_RUN)
+  bool dry_run = false, async_alloc = false;
   cudaGraphExec_t graph = nullptr;  // full job from the first pass (IG_F_GRAPH)
   cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
   bool check_overflow = false;
 };
 
 namespace {
+
+// Every device allocation of a plan goes through here: counted, skipped in a
+// dry run, stream-ordered with IG_F_ASYNC_ALLOC.
+template <class T>
+cudaError_t dev_alloc(ig_plan* pl, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+  pl->dev_bytes += bytes;
+  if (pl->dry_run) return cudaSuccess;
+  if (pl->async_alloc) return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, pl->stream);
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 uint32_t row_bytes_for(const ig_plan* pl, uint32_t j) { return (j * pl->sb + 7) / 8; }
 
@@ -151,7 +159,10 @@ void release(ig_plan* pl) {
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
                   pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank};
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q) {
+      if (pl->async_alloc) cudaFreeAsync(q, pl->stream);
+      else cudaFree(q);
+    }
   if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
   delete pl;
 }
@@ -292,6 +303,62 @@ ig_status read_status(ig_plan* pl) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Asynchronous plan steps for the serving engine (same library): nothing here
+// synchronises; completion is signalled by the event each step records.
+namespace ig {
+
+bool plan_passes_done(const ig_plan* pl) { return pl->next_j > pl->p.n; }
+
+uint32_t plan_row_bytes(const ig_plan* pl) { return row_bytes_for(pl, pl->p.n); }
+
+// Enqueue the next pass, the read-back of its status word, and `ev`.
+ig_status plan_enqueue_next(ig_plan* pl, cudaEvent_t ev) {
+  const uint32_t j = pl->next_j;
+  pl->kernels += enqueue_pass(pl, j, pl->stream);
+  finish_pass_host(pl, j);
+  IG_CUDA(cudaMemcpyAsync(pl->h_ctl, pl->ctl, sizeof(PassCtl), cudaMemcpyDeviceToHost, pl->stream));
+  IG_CUDA(cudaEventRecord(ev, pl->stream));
+  IG_CUDA(cudaGetLastError());
+  return IG_OK;
+}
+
+// Status of the last enqueued pass; call once its event has completed.
+ig_status plan_last_status(ig_plan* pl) {
+  const uint32_t st = pl->h_ctl->status;
+  pl->nsel_last = pl->h_ctl->nsel;
+  if (st & kStCountOverflow) return fail(IG_EOVERFLOW, "a 32-bit count overflowed");
+  if (st & kStListFull) return fail(IG_ETABLE_FULL, "a survivor list exceeded its capacity (raise list_pct)");
+  if (st & (kStSetFull | kStTableFull)) return fail(IG_ETABLE_FULL, "a device hash table filled up");
+  if (st) return fail(IG_ECUDA, "device status error");
+  return IG_OK;
+}
+
+// Enqueue the final top-k into PINNED host buffers, and `ev`; *rows is known
+// at once (from the last status).
+ig_status plan_enqueue_topk(ig_plan* pl, uint8_t* keys_host, uint64_t* counts_host, uint32_t cap, uint32_t* rows,
+                            cudaEvent_t ev) {
+  const uint32_t j = pl->last_j;
+  const uint32_t r = std::min(std::min(pl->p.k, cap), pl->nsel_last);
+  *rows = r;
+  cudaStream_t s = pl->stream;
+  if (r) {
+    launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
+                         pl->shist, s);
+    const uint32_t rb = row_bytes_for(pl, j);
+    launch_write_topk(pl->sel_hist, pl->p.candidates, pl->b, pl->sel_count, pl->sidx[0], pl->ctl, pl->sb, j, rb, r,
+                      pl->out_keys, pl->out_counts, s);
+    pl->kernels += 14;
+    IG_CUDA(cudaMemcpyAsync(keys_host, pl->out_keys, (size_t)r * rb, cudaMemcpyDeviceToHost, s));
+    IG_CUDA(cudaMemcpyAsync(counts_host, pl->out_counts, (size_t)r * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  }
+  IG_CUDA(cudaEventRecord(ev, s));
+  IG_CUDA(cudaGetLastError());
+  return IG_OK;
+}
+
+}  // namespace ig
+
 extern "C" {
 
 const char* intergrams_last_error(void) { return g_last_error.c_str(); }
@@ -320,6 +387,8 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   pl->sigma = 1u << pl->sb;
   pl->b = std::min(p->base_n, p->n);
   pl->next_j = pl->b;
+  pl->dry_run = (p->flags & IG_F_DRY_RUN) != 0;
+  pl->async_alloc = (p->flags & IG_F_ASYNC_ALLOC) != 0;
 
   auto bail = [&](ig_status st) {
     release(pl);
@@ -338,7 +407,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
 
   // offsets on the host
   pl->h_offsets.resize((size_t)m + 1);
-  if (p->flags & IG_F_HOST_INPUT) {
+  if (p->flags & (IG_F_HOST_INPUT | IG_F_OFFSETS_HOST)) {
     std::memcpy(pl->h_offsets.data(), offsets, sizeof(uint64_t) * ((size_t)m + 1));
   } else {
     PLAN_CUDA(cudaMemcpyAsync(pl->h_offsets.data(), offsets, sizeof(uint64_t) * ((size_t)m + 1),
@@ -354,16 +423,21 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   pl->data_bytes = (pl->total_syms * pl->sb + 7) / 8;
   if (pl->data_bytes && !data) return bail(fail(IG_EINVAL, "data is NULL"));
 
-  if (p->flags & IG_F_HOST_INPUT) {
-    PLAN_CUDA(dev_alloc(&pl->own_data, pl->data_bytes));
-    PLAN_CUDA(dev_alloc(&pl->own_offsets, (size_t)m + 1));
-    if (pl->data_bytes)
-      PLAN_CUDA(cudaMemcpyAsync(pl->own_data, data, pl->data_bytes, cudaMemcpyHostToDevice, pl->stream));
-    PLAN_CUDA(cudaMemcpyAsync(pl->own_offsets, pl->h_offsets.data(), sizeof(uint64_t) * ((size_t)m + 1),
-                              cudaMemcpyHostToDevice, pl->stream));
-    pl->data = pl->own_data;
+  if (p->flags & (IG_F_HOST_INPUT | IG_F_OFFSETS_HOST)) {
+    if (p->flags & IG_F_HOST_INPUT) {
+      PLAN_CUDA(dev_alloc(pl, &pl->own_data, pl->data_bytes));
+      if (pl->data_bytes && !pl->dry_run)
+        PLAN_CUDA(cudaMemcpyAsync(pl->own_data, data, pl->data_bytes, cudaMemcpyHostToDevice, pl->stream));
+      pl->data = pl->own_data;
+      pl->host_data = data;
+    } else {
+      pl->data = reinterpret_cast<const uint8_t*>(data);
+    }
+    PLAN_CUDA(dev_alloc(pl, &pl->own_offsets, (size_t)m + 1));
+    if (!pl->dry_run)
+      PLAN_CUDA(cudaMemcpyAsync(pl->own_offsets, pl->h_offsets.data(), sizeof(uint64_t) * ((size_t)m + 1),
+                                cudaMemcpyHostToDevice, pl->stream));
     pl->offsets = pl->own_offsets;
-    pl->host_data = data;
   } else {
     pl->data = reinterpret_cast<const uint8_t*>(data);
     pl->offsets = offsets;
@@ -453,33 +527,34 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   }
   pl->ntiles = tile_base[m];
 
-  PLAN_CUDA(dev_alloc(&pl->counts, nslots));
+  PLAN_CUDA(dev_alloc(pl, &pl->counts, nslots));
   pl->alive_words = (pl->total_syms + 31) / 32 + 1;
   if (p->n >= pl->b + 2) {
-    PLAN_CUDA(dev_alloc(&pl->alive[0], pl->alive_words));
-    PLAN_CUDA(dev_alloc(&pl->alive[1], pl->alive_words));
+    PLAN_CUDA(dev_alloc(pl, &pl->alive[0], pl->alive_words));
+    PLAN_CUDA(dev_alloc(pl, &pl->alive[1], pl->alive_words));
   }
   if (pl->hot_log2) {
-    PLAN_CUDA(dev_alloc(&pl->hot, (size_t)1 << pl->hot_log2));
-    PLAN_CUDA(dev_alloc(&pl->hot_pick, (size_t)1 << pl->hot_log2));
+    PLAN_CUDA(dev_alloc(pl, &pl->hot, (size_t)1 << pl->hot_log2));
+    PLAN_CUDA(dev_alloc(pl, &pl->hot_pick, (size_t)1 << pl->hot_log2));
   }
-  PLAN_CUDA(dev_alloc(&pl->table, (size_t)1 << pl->table_log2));
-  PLAN_CUDA(dev_alloc(&pl->keys[0], p->candidates));
-  PLAN_CUDA(dev_alloc(&pl->keys[1], p->candidates));
-  PLAN_CUDA(dev_alloc(&pl->sel_hist, (size_t)(p->n - pl->b + 1) * p->candidates));
-  PLAN_CUDA(dev_alloc(&pl->sel_count, p->candidates));
-  PLAN_CUDA(dev_alloc(&pl->rank, p->candidates));
-  PLAN_CUDA(dev_alloc(&pl->hist, (size_t)kMaxLevels * kHistBins));
-  PLAN_CUDA(dev_alloc(&pl->blk, (size_t)2 * pl->G));
-  PLAN_CUDA(dev_alloc(&pl->sidx[0], pl->sort_cap));
-  PLAN_CUDA(dev_alloc(&pl->sidx[1], pl->sort_cap));
-  PLAN_CUDA(dev_alloc(&pl->skey[0], pl->sort_cap));
-  PLAN_CUDA(dev_alloc(&pl->skey[1], pl->sort_cap));
-  PLAN_CUDA(dev_alloc(&pl->shist, (size_t)kSortDigits * sortG));
-  if (pl->spill_cap) PLAN_CUDA(dev_alloc(&pl->spill, (size_t)pl->scan_grid * 2 * pl->spill_cap));
-  PLAN_CUDA(dev_alloc(&pl->d_tile_base, (size_t)m + 1));
-  PLAN_CUDA(cudaMemcpyAsync(pl->d_tile_base, tile_base.data(), sizeof(uint32_t) * ((size_t)m + 1),
-                            cudaMemcpyHostToDevice, pl->stream));
+  PLAN_CUDA(dev_alloc(pl, &pl->table, (size_t)1 << pl->table_log2));
+  PLAN_CUDA(dev_alloc(pl, &pl->keys[0], p->candidates));
+  PLAN_CUDA(dev_alloc(pl, &pl->keys[1], p->candidates));
+  PLAN_CUDA(dev_alloc(pl, &pl->sel_hist, (size_t)(p->n - pl->b + 1) * p->candidates));
+  PLAN_CUDA(dev_alloc(pl, &pl->sel_count, p->candidates));
+  PLAN_CUDA(dev_alloc(pl, &pl->rank, p->candidates));
+  PLAN_CUDA(dev_alloc(pl, &pl->hist, (size_t)kMaxLevels * kHistBins));
+  PLAN_CUDA(dev_alloc(pl, &pl->blk, (size_t)2 * pl->G));
+  PLAN_CUDA(dev_alloc(pl, &pl->sidx[0], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(pl, &pl->sidx[1], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(pl, &pl->skey[0], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(pl, &pl->skey[1], pl->sort_cap));
+  PLAN_CUDA(dev_alloc(pl, &pl->shist, (size_t)kSortDigits * sortG));
+  if (pl->spill_cap) PLAN_CUDA(dev_alloc(pl, &pl->spill, (size_t)pl->scan_grid * 2 * pl->spill_cap));
+  PLAN_CUDA(dev_alloc(pl, &pl->d_tile_base, (size_t)m + 1));
+  if (!pl->dry_run)
+    PLAN_CUDA(cudaMemcpyAsync(pl->d_tile_base, tile_base.data(), sizeof(uint32_t) * ((size_t)m + 1),
+                              cudaMemcpyHostToDevice, pl->stream));
   if (any_chain) {
     // default capacity: every window when two such lists use at most 25% of the
     // free device memory, else list_pct (25%) of the windows
@@ -491,12 +566,18 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
     }
     pl->list_cap = std::max<uint64_t>(1u << 16, pl->total_syms * list_pct / 100);
     for (int q = 0; q < 2; ++q) {
-      PLAN_CUDA(dev_alloc(&pl->lists[q], pl->list_cap));
-      PLAN_CUDA(dev_alloc(&pl->list_off[q], std::max<size_t>((size_t)pl->ntiles * pl->runs_per_tile, 1)));
-      PLAN_CUDA(dev_alloc(&pl->list_cnt[q], std::max<size_t>((size_t)pl->ntiles * pl->runs_per_tile, 1)));
+      PLAN_CUDA(dev_alloc(pl, &pl->lists[q], pl->list_cap));
+      PLAN_CUDA(dev_alloc(pl, &pl->list_off[q], std::max<size_t>((size_t)pl->ntiles * pl->runs_per_tile, 1)));
+      PLAN_CUDA(dev_alloc(pl, &pl->list_cnt[q], std::max<size_t>((size_t)pl->ntiles * pl->runs_per_tile, 1)));
     }
   }
-  PLAN_CUDA(dev_alloc(&pl->ctl, 1));
+  PLAN_CUDA(dev_alloc(pl, &pl->ctl, 1));
+  if (pl->dry_run) {  // also count the result buffers and the schedule allocated below
+    pl->dev_bytes += (((uint64_t)p->k * row_bytes_for(pl, p->n) + 8 + 255) & ~255ull) +
+                     (((uint64_t)p->k * 8 + 255) & ~255ull) + (((uint64_t)m * 4 + 255) & ~255ull);
+    *out = pl;
+    return IG_OK;
+  }
   PLAN_CUDA(cudaMemsetAsync(pl->ctl, 0, sizeof(PassCtl), pl->stream));
   PLAN_CUDA(cudaMallocHost(reinterpret_cast<void**>(&pl->h_ctl), sizeof(PassCtl)));
   if (p->flags & IG_F_TIMING) {
@@ -507,8 +588,8 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
     }
   }
   pl->out_cap = p->k;
-  PLAN_CUDA(dev_alloc(&pl->out_keys, (size_t)pl->out_cap * row_bytes_for(pl, p->n) + 8));
-  PLAN_CUDA(dev_alloc(&pl->out_counts, pl->out_cap));
+  PLAN_CUDA(dev_alloc(pl, &pl->out_keys, (size_t)pl->out_cap * row_bytes_for(pl, p->n) + 8));
+  PLAN_CUDA(dev_alloc(pl, &pl->out_counts, pl->out_cap));
 
   // schedule: sequences longest first (ties by index)
   std::vector<uint32_t> order(m);
@@ -516,9 +597,11 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
     return pl->h_offsets[x + 1] - pl->h_offsets[x] > pl->h_offsets[y + 1] - pl->h_offsets[y];
   });
-  PLAN_CUDA(dev_alloc(&pl->d_order, m));
+  PLAN_CUDA(dev_alloc(pl, &pl->d_order, m));
   if (m) PLAN_CUDA(cudaMemcpyAsync(pl->d_order, order.data(), sizeof(uint32_t) * m, cudaMemcpyHostToDevice, pl->stream));
-  PLAN_CUDA(cudaStreamSynchronize(pl->stream));
+  // host staging above is pageable, so the copies have consumed it already;
+  // the synchronisation only makes plan creation a clean point for callers
+  if (!pl->async_alloc) PLAN_CUDA(cudaStreamSynchronize(pl->stream));
 #undef PLAN_CUDA
   *out = pl;
   return IG_OK;
@@ -614,6 +697,12 @@ ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out, 
   return IG_OK;
 }
 
+ig_status intergrams_plan_device_bytes(const ig_plan* pl, uint64_t* bytes) {
+  if (!pl || !bytes) return fail(IG_EINVAL, "plan or bytes is NULL");
+  *bytes = pl->dev_bytes;
+  return IG_OK;
+}
+
 ig_status intergrams_stats(ig_plan* pl, ig_pass_stats* out) {
   if (!pl || !out) return fail(IG_EINVAL, "plan or out is NULL");
   std::memset(out, 0, sizeof(*out));
@@ -649,7 +738,7 @@ ig_status intergrams_timings(ig_plan* pl, float* scan_ms, float* pass_ms, uint32
 
 void intergrams_free(ig_plan* pl) {
   if (!pl) return;
-  cudaStreamSynchronize(pl->stream);
+  if (!pl->dry_run) cudaStreamSynchronize(pl->stream);
   release(pl);
 }
 

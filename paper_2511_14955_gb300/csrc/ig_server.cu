@@ -1,0 +1,351 @@
+// Serving engine: continuous batching of top-k n-gram jobs on one GPU.
+//
+// Callers submit jobs (a corpus already on the device, host offsets, the
+// job's parameters). A scheduler thread admits pending jobs in arrival order
+// whenever a slot is free and the job's tables fit the device-memory budget
+// (sizes come from a dry-run plan), gives each admitted job its own plan and
+// stream, and then advances every active job one pass at a time: whenever a
+// job's previous step has completed on the GPU it enqueues the job's next
+// pass (or its final top-k). Jobs at different passes therefore have work in
+// flight on the device at the same time, each job's candidate and count
+// tables stay resident between its passes, and a job that arrives while
+// others run is admitted as soon as memory and a slot free up. With
+// max_active = 1 the same engine runs one job per launch, in order.
+//
+// A job's result does not depend on what else runs: each job owns every
+// table it touches (its plan), and the kernels are deterministic.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ig_internal.cuh"
+
+namespace ig {
+bool plan_passes_done(const ig_plan* pl);
+uint32_t plan_row_bytes(const ig_plan* pl);
+ig_status plan_enqueue_next(ig_plan* pl, cudaEvent_t ev);
+ig_status plan_last_status(ig_plan* pl);
+ig_status plan_enqueue_topk(ig_plan* pl, uint8_t* keys_host, uint64_t* counts_host, uint32_t cap, uint32_t* rows,
+                            cudaEvent_t ev);
+void set_last_error(const std::string& msg);
+}  // namespace ig
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum JobState { kPending = 0, kPasses = 1, kTopk = 2, kDone = 3 };
+
+struct Job {
+  uint64_t id = 0;
+  ig_params p{};
+  ig_tuning t{};
+  bool has_tuning = false;
+  const void* data = nullptr;
+  std::vector<uint64_t> offsets;
+  uint32_t m = 0;
+  uint64_t bytes = 0;  // device bytes charged against the budget
+  ig_plan* plan = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  uint8_t* keys_pinned = nullptr;
+  uint64_t* counts_pinned = nullptr;
+  int state = kPending;
+  bool inflight = false;
+  ig_status status = IG_OK;
+  std::string err;
+  std::vector<uint8_t> keys;
+  std::vector<uint64_t> counts;
+  uint32_t rows = 0, row_bytes = 0;
+  Clock::time_point t_submit, t_admit, t_done;
+};
+
+}  // namespace
+
+struct ig_server {
+  ig_server_config cfg{};
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job*> pending;
+  std::map<uint64_t, Job*> jobs;
+  uint64_t next_id = 1;
+  bool stop = false;
+  uint32_t active = 0, peak_active = 0;
+  uint64_t mem_used = 0, peak_mem = 0, submitted = 0, completed = 0, failed = 0;
+  std::thread worker;
+};
+
+namespace {
+
+void release_job_resources(Job* jb) {
+  if (jb->plan) intergrams_free(jb->plan);  // synchronises the job's stream
+  jb->plan = nullptr;
+  if (jb->ev) cudaEventDestroy(jb->ev);
+  jb->ev = nullptr;
+  if (jb->stream) cudaStreamDestroy(jb->stream);
+  jb->stream = nullptr;
+  if (jb->keys_pinned) cudaFreeHost(jb->keys_pinned);
+  jb->keys_pinned = nullptr;
+  if (jb->counts_pinned) cudaFreeHost(jb->counts_pinned);
+  jb->counts_pinned = nullptr;
+}
+
+void finish_job(ig_server* sv, Job* jb, ig_status st, const std::string& err) {
+  if (st == IG_OK && jb->rows) {
+    jb->keys.assign(jb->keys_pinned, jb->keys_pinned + (size_t)jb->rows * jb->row_bytes);
+    jb->counts.assign(jb->counts_pinned, jb->counts_pinned + jb->rows);
+  }
+  release_job_resources(jb);
+  std::lock_guard<std::mutex> lock(sv->mu);
+  jb->status = st;
+  jb->err = err;
+  jb->state = kDone;
+  jb->t_done = Clock::now();
+  sv->mem_used -= jb->bytes;
+  sv->active -= 1;
+  if (st == IG_OK) sv->completed += 1;
+  else sv->failed += 1;
+  sv->cv_done.notify_all();
+  sv->cv_work.notify_all();
+}
+
+// Create the job's plan, stream and result buffers (scheduler thread).
+ig_status admit_job(Job* jb, std::string* err) {
+  if (cudaStreamCreateWithFlags(&jb->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&jb->ev, cudaEventDisableTiming) != cudaSuccess) {
+    *err = "stream/event creation failed";
+    return IG_ECUDA;
+  }
+  ig_params p = jb->p;
+  p.flags = (p.flags & ~(IG_F_HOST_INPUT | IG_F_GRAPH | IG_F_DRY_RUN)) | IG_F_OFFSETS_HOST | IG_F_ASYNC_ALLOC;
+  ig_status st = intergrams_plan(&p, jb->data, jb->offsets.data(), jb->m, jb->stream,
+                                 jb->has_tuning ? &jb->t : nullptr, &jb->plan);
+  if (st != IG_OK) {
+    *err = intergrams_last_error();
+    return st;
+  }
+  jb->row_bytes = ig::plan_row_bytes(jb->plan);
+  const size_t kb = std::max<size_t>((size_t)jb->p.k * jb->row_bytes, 1);
+  if (cudaMallocHost(reinterpret_cast<void**>(&jb->keys_pinned), kb) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&jb->counts_pinned), sizeof(uint64_t) * jb->p.k) != cudaSuccess) {
+    *err = "pinned host allocation failed";
+    return IG_ENOMEM;
+  }
+  return IG_OK;
+}
+
+void scheduler(ig_server* sv) {
+  cudaSetDevice(sv->device);
+  std::vector<Job*> running;
+  for (;;) {
+    std::vector<Job*> admit;
+    {
+      std::unique_lock<std::mutex> lock(sv->mu);
+      if (sv->stop && sv->pending.empty() && running.empty()) break;
+      // admission: arrival order, while a slot is free and the budget allows
+      while (!sv->pending.empty() && sv->active < sv->cfg.max_active) {
+        Job* jb = sv->pending.front();
+        if (sv->mem_used + jb->bytes > sv->cfg.mem_budget && sv->active > 0) break;
+        sv->pending.pop_front();
+        sv->mem_used += jb->bytes;
+        sv->peak_mem = std::max(sv->peak_mem, sv->mem_used);
+        sv->active += 1;
+        sv->peak_active = std::max(sv->peak_active, sv->active);
+        admit.push_back(jb);
+      }
+      if (running.empty() && admit.empty()) {
+        sv->cv_work.wait_for(lock, std::chrono::milliseconds(2));
+        continue;
+      }
+    }
+    for (Job* jb : admit) {
+      jb->t_admit = Clock::now();
+      std::string err;
+      const ig_status st = admit_job(jb, &err);
+      if (st != IG_OK) finish_job(sv, jb, st, err);
+      else running.push_back(jb);
+    }
+    bool progressed = !admit.empty();
+    for (Job* jb : running) {
+      if (jb->inflight) {
+        const cudaError_t q = cudaEventQuery(jb->ev);
+        if (q == cudaErrorNotReady) continue;
+        jb->inflight = false;
+        progressed = true;
+        if (q != cudaSuccess) {
+          finish_job(sv, jb, IG_ECUDA, cudaGetErrorString(q));
+          continue;
+        }
+        if (jb->state == kPasses) {
+          const ig_status st = ig::plan_last_status(jb->plan);
+          if (st != IG_OK) {
+            finish_job(sv, jb, st, intergrams_last_error());
+            continue;
+          }
+        } else if (jb->state == kTopk) {
+          finish_job(sv, jb, IG_OK, "");
+          continue;
+        }
+      }
+      // the job's previous step is complete: enqueue its next one
+      ig_status st;
+      if (!ig::plan_passes_done(jb->plan)) {
+        jb->state = kPasses;
+        st = ig::plan_enqueue_next(jb->plan, jb->ev);
+      } else {
+        jb->state = kTopk;
+        st = ig::plan_enqueue_topk(jb->plan, jb->keys_pinned, jb->counts_pinned, jb->p.k, &jb->rows, jb->ev);
+      }
+      if (st != IG_OK) {
+        finish_job(sv, jb, st, intergrams_last_error());
+        continue;
+      }
+      jb->inflight = true;
+      progressed = true;
+    }
+    running.erase(std::remove_if(running.begin(), running.end(), [](Job* jb) { return jb->state == kDone; }),
+                  running.end());
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+ig_status intergrams_server_create(const ig_server_config* cfg, ig_server** out) {
+  ig::set_last_error("");
+  if (!out) return IG_EINVAL;
+  *out = nullptr;
+  ig_server* sv = new (std::nothrow) ig_server();
+  if (!sv) return IG_ENOMEM;
+  if (cfg) sv->cfg = *cfg;
+  if (sv->cfg.max_active == 0) sv->cfg.max_active = 8;
+  if (cudaGetDevice(&sv->device) != cudaSuccess) {
+    delete sv;
+    return IG_ECUDA;
+  }
+  if (sv->cfg.mem_budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      delete sv;
+      return IG_ECUDA;
+    }
+    sv->cfg.mem_budget = (uint64_t)(free_b * 0.8);
+  }
+  // keep freed job tables cached in the stream-ordered pool between jobs
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  sv->worker = std::thread(scheduler, sv);
+  *out = sv;
+  return IG_OK;
+}
+
+ig_status intergrams_server_submit(ig_server* sv, const ig_params* p, const void* data, const uint64_t* offsets,
+                                   uint32_t m, const ig_tuning* tuning, uint64_t* job_id) {
+  ig::set_last_error("");
+  if (!sv || !p || !offsets || !job_id) {
+    ig::set_last_error("NULL argument");
+    return IG_EINVAL;
+  }
+  // size the job's tables with a dry-run plan (also validates the arguments)
+  ig_params dp = *p;
+  dp.flags = (dp.flags & ~(IG_F_HOST_INPUT | IG_F_GRAPH)) | IG_F_OFFSETS_HOST | IG_F_DRY_RUN;
+  ig_plan* dry = nullptr;
+  ig_status st = intergrams_plan(&dp, data, offsets, m, nullptr, tuning, &dry);
+  if (st != IG_OK) return st;
+  uint64_t bytes = 0;
+  intergrams_plan_device_bytes(dry, &bytes);
+  intergrams_free(dry);
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (bytes > sv->cfg.mem_budget) {
+    ig::set_last_error("job needs more device memory than the server budget");
+    return IG_ENOMEM;
+  }
+  Job* jb = new (std::nothrow) Job();
+  if (!jb) return IG_ENOMEM;
+  jb->id = sv->next_id++;
+  jb->p = *p;
+  if (tuning) {
+    jb->t = *tuning;
+    jb->has_tuning = true;
+  }
+  jb->data = data;
+  jb->offsets.assign(offsets, offsets + (size_t)m + 1);
+  jb->m = m;
+  jb->bytes = bytes;
+  jb->t_submit = Clock::now();
+  sv->jobs[jb->id] = jb;
+  sv->pending.push_back(jb);
+  sv->submitted += 1;
+  sv->cv_work.notify_all();
+  *job_id = jb->id;
+  return IG_OK;
+}
+
+ig_status intergrams_server_wait(ig_server* sv, uint64_t job_id, int64_t timeout_us, uint8_t* keys_out,
+                                 uint64_t* counts_out, uint32_t capacity, uint32_t* k_out, double* latency_s) {
+  ig::set_last_error("");
+  if (!sv || !k_out) return IG_EINVAL;
+  *k_out = 0;
+  std::unique_lock<std::mutex> lock(sv->mu);
+  auto it = sv->jobs.find(job_id);
+  if (it == sv->jobs.end()) {
+    ig::set_last_error("unknown job id");
+    return IG_EINVAL;
+  }
+  Job* jb = it->second;
+  auto done = [&] { return jb->state == kDone; };
+  if (timeout_us < 0) sv->cv_done.wait(lock, done);
+  else if (!sv->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done)) return IG_ETIMEOUT;
+  const uint32_t r = std::min(capacity, jb->rows);
+  if (keys_out && r) std::memcpy(keys_out, jb->keys.data(), (size_t)r * jb->row_bytes);
+  if (counts_out && r) std::memcpy(counts_out, jb->counts.data(), sizeof(uint64_t) * r);
+  *k_out = jb->status == IG_OK ? r : 0;
+  if (latency_s) *latency_s = std::chrono::duration<double>(jb->t_done - jb->t_submit).count();
+  const ig_status st = jb->status;
+  if (st != IG_OK) ig::set_last_error(jb->err);
+  sv->jobs.erase(it);
+  delete jb;
+  return st;
+}
+
+ig_status intergrams_server_stats(ig_server* sv, ig_server_stats* out) {
+  if (!sv || !out) return IG_EINVAL;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  out->submitted = sv->submitted;
+  out->completed = sv->completed;
+  out->failed = sv->failed;
+  out->active = sv->active;
+  out->peak_active = sv->peak_active;
+  out->pending = (uint32_t)sv->pending.size();
+  out->mem_used = sv->mem_used;
+  out->peak_mem = sv->peak_mem;
+  out->mem_budget = sv->cfg.mem_budget;
+  return IG_OK;
+}
+
+void intergrams_server_destroy(ig_server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stop = true;
+    sv->cv_work.notify_all();
+  }
+  if (sv->worker.joinable()) sv->worker.join();
+  for (auto& kv : sv->jobs) delete kv.second;
+  delete sv;
+}
+
+}  // extern "C"
