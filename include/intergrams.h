@@ -116,6 +116,18 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
                           uint32_t m, void* stream, const ig_tuning* tuning, ig_plan** out);
 
 /*
+ * intergrams_autotune - pick the tuning knobs for a job by timing a few
+ * candidate settings on a prefix of the sequences of about sample_bytes
+ * (0 = 256 MiB); every candidate must return byte-identical results (else
+ * IG_ESTATE). Arguments as for intergrams_plan; out receives the fastest
+ * knobs, best_ms (optional) their job time on the sample. Results are cached
+ * per process. intergrams_plan with IG_F_AUTOTUNE calls this for the knobs
+ * left at 0. Synchronises the stream.
+ */
+ig_status intergrams_autotune(const ig_params* p, const void* data, const uint64_t* offsets, uint32_t m,
+                              void* stream, uint64_t sample_bytes, ig_tuning* out, float* best_ms);
+
+/*
  * intergrams_pass - run the next pass (the dense base pass first, then the
  * candidate passes j = base_n+1 .. n, paper Algorithm 3) and its selection.
  *   j_done : receives the n-gram length j of the pass just run.

@@ -29,7 +29,7 @@ EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_r
            "intergrams_stats", "intergrams_timings", "intergrams_free", "intergrams_last_error",
            "intergrams_dense_topk_static", "intergrams_plan_device_bytes", "intergrams_server_create",
            "intergrams_server_submit", "intergrams_server_wait", "intergrams_server_stats",
-           "intergrams_server_destroy"]
+           "intergrams_server_destroy", "intergrams_autotune"]
 
 
 class IgParams(ctypes.Structure):
@@ -117,6 +117,9 @@ def load(build_if_missing: bool = True):
     lib.intergrams_server_stats.argtypes = [P, ctypes.POINTER(IgServerStats)]
     lib.intergrams_server_destroy.restype = None
     lib.intergrams_server_destroy.argtypes = [P]
+    lib.intergrams_autotune.restype = ctypes.c_int
+    lib.intergrams_autotune.argtypes = [ctypes.POINTER(IgParams), P, P, U32, P, ctypes.c_uint64,
+                                        ctypes.POINTER(IgTuning), ctypes.POINTER(ctypes.c_float)]
     lib.intergrams_last_error.restype = ctypes.c_char_p
     lib.intergrams_last_error.argtypes = []
     _lib = lib
@@ -148,10 +151,12 @@ class Plan:
 
     def __init__(self, data, offsets, *, n: int, k: int, candidates: int, base_n: int = 3,
                  symbol_bits: int = 8, count_mode: int = COUNT_ONCE_PER_SEQUENCE, graph: bool = False,
-                 host_input: bool = False, timing: bool = False, stream=None, tuning: dict | None = None):
+                 host_input: bool = False, timing: bool = False, autotune: bool = False, stream=None,
+                 tuning: dict | None = None):
         self._lib = load()
         self._h = ctypes.c_void_p(None)
-        flags = (F_GRAPH if graph else 0) | (F_HOST_INPUT if host_input else 0) | (F_TIMING if timing else 0)
+        flags = ((F_GRAPH if graph else 0) | (F_HOST_INPUT if host_input else 0) | (F_TIMING if timing else 0)
+                 | (F_AUTOTUNE if autotune else 0))
         self.params = IgParams(n, k, candidates, base_n, symbol_bits, count_mode, flags)
         tun = IgTuning(**(tuning or {}))
         if host_input:
@@ -318,3 +323,21 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def autotune(data, offsets, *, n: int, k: int, candidates: int, base_n: int = 3, symbol_bits: int = 8,
+             count_mode: int = COUNT_ONCE_PER_SEQUENCE, sample_bytes: int = 0, stream=None):
+    """intergrams_autotune: (best tuning dict, its job time in ms on the sample)."""
+    lib = load()
+    params = IgParams(n, k, candidates, base_n, symbol_bits, count_mode, 0)
+    out = IgTuning()
+    best = ctypes.c_float(0.0)
+    if stream is None:
+        import torch
+        stream_ptr = torch.cuda.current_stream().cuda_stream
+    else:
+        stream_ptr = getattr(stream, "cuda_stream", stream)
+    _check(lib, lib.intergrams_autotune(ctypes.byref(params), _ptr(data), _ptr(offsets), len(offsets) - 1,
+                                        stream_ptr, int(sample_bytes), ctypes.byref(out), ctypes.byref(best)),
+           "intergrams_autotune")
+    return {f: getattr(out, f) for f, _ in IgTuning._fields_}, best.value

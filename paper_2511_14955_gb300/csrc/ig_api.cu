@@ -378,6 +378,21 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (p->count_mode > 1) return fail(IG_EINVAL, "count_mode must be 0 or 1");
   if (!offsets) return fail(IG_EINVAL, "offsets is NULL");
 
+  // IG_F_AUTOTUNE: knobs left at 0 come from the autotuner (timed on a sample)
+  ig_tuning tuned{};
+  if ((p->flags & IG_F_AUTOTUNE) && !(p->flags & IG_F_DRY_RUN)) {
+    ig_params ap = *p;
+    ap.flags &= ~(IG_F_AUTOTUNE | IG_F_GRAPH | IG_F_TIMING);
+    ig_tuning best{};
+    const ig_status ast = intergrams_autotune(&ap, data, offsets, m, stream, 0, &best, nullptr);
+    if (ast != IG_OK) return ast;
+    tuned = tuning ? *tuning : ig_tuning{};
+    uint32_t* dst = &tuned.ctas_per_sm;
+    const uint32_t* src = &best.ctas_per_sm;
+    for (size_t i = 0; i < sizeof(ig_tuning) / sizeof(uint32_t); ++i)
+      if (dst[i] == 0) dst[i] = src[i];
+    tuning = &tuned;
+  }
   ig_plan* pl = new (std::nothrow) ig_plan();
   if (!pl) return fail(IG_ENOMEM, "host allocation failed");
   pl->p = *p;

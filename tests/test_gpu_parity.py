@@ -214,6 +214,18 @@ def test_timing_events_in_both_launch_modes():
         pl.close()
 
 
+def test_autotune_picks_valid_knobs_and_keeps_results():
+    data, off, _ = synth.make_corpus("malware_8gb", m=50, max_len=64 * 1024, seed=13)
+    d, o = dev(data, off)
+    best, ms = B.autotune(d, o, n=7, k=500, candidates=2000, base_n=3, sample_bytes=1 << 20)
+    assert best["threads"] in (256, 512, 1024) and best["words_per_thread"] % 2 == 1 and ms > 0
+    ek, ec = O.intergrams(data, off, 7, 500, 2000, base_n=3)
+    with B.Plan(d, o, n=7, k=500, candidates=2000, base_n=3, autotune=True) as pl:
+        pl.run()
+        gk, gc, _ = pl.topk()
+    assert np.array_equal(gk, ek) and np.array_equal(gc, ec)
+
+
 def test_repeated_runs_identical():
     data, off, _ = synth.make_corpus("malware_8gb", m=40, max_len=64 * 1024, seed=3)
     d, o = dev(data, off)
