@@ -43,9 +43,14 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--m", type=int, default=None, help="override the number of sequences (smaller runs)")
+    ap.add_argument("--max-len", type=int, default=None,
+                    help="clamp sequence lengths (small cases for profiler captures)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--cpu-seqs", type=int, default=24, help="sequences in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=120, help="jobs in the serving leg (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -177,6 +182,22 @@ def cpu_baseline(name: str, seed: int, nseq: int, p):
     return {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample}, np
 
 
+def serving_leg(args, seed):
+    """Poisson job stream (20 jobs/s; corpora of the 2 MiB workload's byte law,
+    total sizes lognormal with median 64 MB, clamped to [1 MB, 512 MB] here to
+    bound the run; n in {4, 8, 16}; k in {1K, 16K, 256K}; Z = 4k) through the
+    continuous-batching server, and the same stream one job per launch."""
+    from paper_2511_14955_gb300 import serving
+    pool = serving.make_pool(8, seed=seed + 7, hi_bytes=512 << 20)
+    jobs = serving.job_stream(args.serve_jobs, args.serve_rate, len(pool), seed=seed + 11)
+    tun = {"list_pct": 50}
+    batched = serving.run_stream(pool, jobs, max_active=8, tuning=tun)
+    single = serving.run_stream(pool, jobs, max_active=1, tuning=tun)
+    return {"workload": f"{len(jobs)} Poisson jobs at {args.serve_rate:g}/s over {len(pool)} corpora "
+                        f"({sum(int(o[-1]) for _, o in pool) / 1e6:.0f} MB), n in {{4,8,16}}, k in {{1K,16K,256K}}",
+            "continuous_batching": batched, "one_job_per_launch": single}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -223,6 +244,8 @@ def main(argv=None):
     w = synth.WORKLOADS[args.workload]
     seed = rank_seed(args.seed, rank)
     L = synth.lengths_for(w, seed, args.m)
+    if args.max_len:
+        L = np.minimum(L, np.uint64(args.max_len))
     off = synth.offsets_from_lengths(L)
     total_syms = int(off[-1])
     nbytes = total_syms if w.symbol_bits == 8 else (total_syms + 3) // 4
@@ -234,7 +257,7 @@ def main(argv=None):
     torch.cuda.synchronize(dev)
 
     npass = passes_of(p)
-    plan = binding.Plan(d_data, d_off, **p, graph=True, timing=True, stream=stream)
+    plan = binding.Plan(d_data, d_off, **p, graph=True, timing=True, autotune=not args.no_autotune, stream=stream)
 
     def barrier():
         if world > 1:
@@ -330,6 +353,8 @@ def main(argv=None):
                      "peak_kind": f"{peak_kind} hbm_gbs", "avg_scan_ms": avg_scan_s * 1e3},
         "clocks": clk,
     }
+    if args.serve_jobs and world == 1:
+        line["serving"] = serving_leg(args, seed)
     if not args.no_cpu_baseline and world == 1:
         cb, _ = cpu_baseline(args.workload, seed, args.cpu_seqs, p)
         line["cpu_baseline"] = cb
