@@ -281,3 +281,70 @@ int oracle_intergrams(const uint8_t* data, const uint64_t* offsets, uint32_t m, 
   free(sym);
   return rc;
 }
+
+/* ----------------------------------------------------- counting given keys */
+
+static uint8_t symbol_at(const uint8_t* data, uint32_t symbol_bits, uint64_t g) {
+  if (symbol_bits == 8) return data[g];
+  return (uint8_t)((data[g >> 2] >> (6 - 2 * (g & 3))) & 3u);
+}
+
+/*
+ * Exact frequency of each of `nkeys` given n-grams (rows of n symbol codes),
+ * by the definitions of Eq. 1 (count_mode 1: every window equal to the key)
+ * and Eq. 2 (count_mode 0: the number of sequences containing the key), over
+ * every window of every sequence. Used to check single outputs of a run on a
+ * corpus too large for the exhaustive count. Keys may repeat; counts_out[i]
+ * is the count of keys[i]. The scan is one pass over the corpus; a bitmap of
+ * the keys' first symbols (2 for bytes, 8 for bases) rejects most windows
+ * before a binary search over the sorted keys.
+ */
+int oracle_count_keys(const uint8_t* data, const uint64_t* offsets, uint32_t m, uint32_t symbol_bits, uint32_t n,
+                      uint32_t count_mode, const uint8_t* keys, uint64_t nkeys, uint64_t* counts_out) {
+  if (n == 0 || !valid_corpus(offsets, m, symbol_bits)) return OR_EINVAL;
+  const uint32_t head = symbol_bits == 8 ? (n < 2 ? n : 2) : (n < 8 ? n : 8);
+  uint8_t* sorted = (uint8_t*)malloc((size_t)(nkeys ? nkeys : 1) * n);
+  uint64_t* cnt = (uint64_t*)calloc(nkeys ? nkeys : 1, sizeof(uint64_t));
+  int64_t* last = (int64_t*)malloc(sizeof(int64_t) * (nkeys ? nkeys : 1));
+  uint8_t* bitmap = (uint8_t*)calloc(8192, 1);
+  uint8_t* win = (uint8_t*)malloc(n);
+  if (!sorted || !cnt || !last || !bitmap || !win) {
+    free(sorted); free(cnt); free(last); free(bitmap); free(win);
+    return OR_ENOMEM;
+  }
+  memcpy(sorted, keys, (size_t)nkeys * n);
+  g_len = n;
+  qsort(sorted, nkeys, n, cmp_key_row);
+  for (uint64_t i = 0; i < nkeys; ++i) last[i] = -1;
+  const uint32_t hb = symbol_bits == 8 ? 8 : 2;
+  for (uint64_t i = 0; i < nkeys; ++i) {
+    uint32_t code = 0;
+    for (uint32_t t = 0; t < head; ++t) code = (code << hb) | sorted[i * n + t];
+    bitmap[code >> 3] |= (uint8_t)(1u << (code & 7));
+  }
+  for (uint32_t s = 0; s < m; ++s) {
+    const uint64_t a = offsets[s], L = offsets[s + 1] - a;
+    if (L < n) continue;
+    for (uint64_t p = a; p + n <= a + L; ++p) {
+      uint32_t code = 0;
+      for (uint32_t t = 0; t < head; ++t) code = (code << hb) | symbol_at(data, symbol_bits, p + t);
+      if (!((bitmap[code >> 3] >> (code & 7)) & 1u)) continue;
+      for (uint32_t t = 0; t < n; ++t) win[t] = symbol_at(data, symbol_bits, p + t);
+      const uint8_t* hit = (const uint8_t*)bsearch(win, sorted, nkeys, n, cmp_key_row);
+      if (!hit) continue;
+      const uint64_t idx = (uint64_t)(hit - sorted) / n;
+      if (count_mode == 1) {
+        cnt[idx] += 1;
+      } else if (last[idx] != (int64_t)s) {
+        last[idx] = s;
+        cnt[idx] += 1;
+      }
+    }
+  }
+  for (uint64_t i = 0; i < nkeys; ++i) {
+    const uint8_t* hit = (const uint8_t*)bsearch(keys + i * n, sorted, nkeys, n, cmp_key_row);
+    counts_out[i] = hit ? cnt[(uint64_t)(hit - sorted) / n] : 0;
+  }
+  free(sorted); free(cnt); free(last); free(bitmap); free(win);
+  return OR_OK;
+}

@@ -56,6 +56,8 @@ def _load():
         lib.oracle_exhaustive.argtypes = [P, P, U32, U32, U32, U32, U64, P, P, P]
         lib.oracle_intergrams.restype = ctypes.c_int
         lib.oracle_intergrams.argtypes = [P, P, U32, U32, U32, U32, U64, U32, U64, U32, P, P, P, P]
+        lib.oracle_count_keys.restype = ctypes.c_int
+        lib.oracle_count_keys.argtypes = [P, P, U32, U32, U32, U32, P, U64, P]
         _lib = lib
     return _lib
 
@@ -110,3 +112,17 @@ def intergrams(data, offsets, n: int, k: int, candidates: int, base_n: int = 3,
     if want_survivors:
         return keys[:r].copy(), counts[:r].copy(), surv.value
     return keys[:r].copy(), counts[:r].copy()
+
+
+def count_keys(data, offsets, keys, count_mode: int = EQ2_ONCE_PER_SEQUENCE, symbol_bits: int = 8):
+    """Exact Eq. 2 (or Eq. 1) counts of the given n-grams (rows of symbol codes)."""
+    lib = _load()
+    data, offsets, m = _prep(data, offsets)
+    keys = np.ascontiguousarray(np.asarray(keys, dtype=np.uint8))
+    nk, n = keys.shape
+    out = np.zeros(max(nk, 1), np.uint64)
+    rc = lib.oracle_count_keys(data.ctypes.data, offsets.ctypes.data, m, symbol_bits, n, count_mode,
+                               keys.ctypes.data, nk, out.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_count_keys failed: {rc}")
+    return out[:nk].copy()

@@ -504,14 +504,15 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   pl->tile_words = (pl->tile_words + 3) & ~3u;
   pl->queue_words = (uint32_t)(((tile_windows + 1) / 2 + 3) & ~3ull);
   const uint32_t alive_tile_words = (uint32_t)((tile_windows + 31) / 32);
-  // (+ the results of one run chunk after the survivor bits)
   auto smem_for = [&](uint32_t set_log2) {
     return ((size_t)4 << set_log2) + (size_t)12 * (pl->hot_log2 ? (1u << pl->hot_log2) : 0u) +
-           (size_t)4 * (pl->tile_words + pl->queue_words + ((alive_tile_words + 3) & ~3u) + kRunChunk);
+           (size_t)4 * (pl->tile_words + pl->queue_words + ((alive_tile_words + 3) & ~3u));
   };
   int max_optin = 0;
   PLAN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
   while (auto_set && t.smem_set_log2 > 8 && smem_for(t.smem_set_log2) + 256 > (size_t)max_optin) --t.smem_set_log2;
+  if (smem_for(t.smem_set_log2) + 256 > (size_t)max_optin)
+    return bail(fail(IG_EINVAL, "tuning needs more shared memory than a CTA can have"));
   pl->t = t;
   pl->scan_threads = (int)t.threads;
   pl->scan_smem = smem_for(t.smem_set_log2);

@@ -18,6 +18,7 @@ constexpr int kMaxLevels = 4;        // threshold-search levels (4096^k >= 2^32 
 constexpr int kSortDigits = 256;     // 8-bit digits of the final stable sort
 constexpr int kSortChunk = 1024;     // elements per one-warp block of the stable sort
 constexpr uint32_t kRunChunk = 2048; // survivors are listed in runs of at most this many candidates
+constexpr uint32_t kMaxRuns = 64;    // runs per tile (tile windows <= 65536 / ... / kRunChunk)
 
 // Sticky device status bits (PassCtl::status).
 enum : uint32_t {

@@ -258,8 +258,9 @@ __device__ void dedupe_spills(const ScanArgs& a, uint32_t S, uint32_t* sset, uin
 template <int SB, bool BASE>
 __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_item, s_nspill, s_qn, s_lcnt, s_ccnt;
-  __shared__ unsigned long long s_lbase;
+  __shared__ uint32_t s_item, s_nspill, s_qn;
+  __shared__ unsigned long long s_run_base[kMaxRuns];
+  __shared__ uint32_t s_run_cnt[kMaxRuns];
   __shared__ unsigned long long s_surv, s_regs;
 
   using S = Sym<SB>;
@@ -278,7 +279,6 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   uint16_t* queue = reinterpret_cast<uint16_t*>(tile + a.tile_words);
   uint32_t* tile_alive = tile + a.tile_words + a.queue_words;
   const uint32_t alive_tile_words = (tile_windows + 31) / 32;
-  uint32_t* res = tile_alive + ((alive_tile_words + 3) & ~3u);   // kRunChunk results of a chunk
   unsigned long long* gset = a.gset ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
   // CTA-private spill list and partition buffer (Eq. 2 without a global set)
   uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
@@ -425,72 +425,68 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           if (tid == 0) s_qn = nwin;
         }
         __syncthreads();
-        // phase B: probe, count, dedupe the queued windows, in chunks of
-        // kRunChunk; a chunk's survivors form one run of the survivor list
+        // survivor list for a chain pass next: run r of this tile takes queue
+        // entries [r * kRunChunk, (r + 1) * kRunChunk); room is reserved for
+        // every candidate up front, survivors are written at once
         const uint32_t qn = s_qn;
         const uint32_t tile_g = a.tile_base[seq] + (uint32_t)(w0 / a.tile_windows);
-        // without a list to write the whole queue is one chunk (no extra barriers)
-        const uint32_t chunk = a.list_out ? kRunChunk : (qn ? qn : 1u);
-        for (uint32_t c0 = 0; c0 < qn; c0 += chunk) {
-          const uint32_t ce = (qn - c0) < chunk ? qn : c0 + chunk;
-          if (tid == 0) s_ccnt = 0;
-          __syncthreads();
-          for (uint32_t qi = c0 + tid; qi < ce; qi += nthr) {
-            const uint32_t w = queue[qi];
-            const uint64_t prefix = tile_key<SB>(tile, sym_off + w, j - 1);
-            const uint32_t last = tile_sym<SB>(tile, sym_off + w + j - 1);
-            uint32_t id = kEmpty32;
-            if (H) {
-              const uint32_t h = hash64_top(prefix, a.hot_log2);
-              if (hot_keys[h] == prefix) id = hot_ids[h];
+        const uint32_t nruns = (qn + kRunChunk - 1) / kRunChunk;
+        if (a.list_out) {
+          if (tid < nruns) {
+            const uint32_t rn = (qn - tid * kRunChunk) < kRunChunk ? qn - tid * kRunChunk : kRunChunk;
+            unsigned long long base = atomicAdd(&a.ctl->list_used, (unsigned long long)rn);
+            if (base + rn > a.list_cap) {
+              atomicOr(&a.ctl->status, kStListFull);
+              base = ~0ull;
             }
-            if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
-            if (a.list_out) res[qi - c0] = id == kEmpty32 ? kEmpty32 : ((id << SB) | last);
-            if (id == kEmpty32) continue;
-            const uint32_t slot = (id << SB) | last;
-            if (a.list_out) atomicAdd(&s_ccnt, 1u);
-            if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
-            ++my_surv;
-            bool count_it = true;
-            if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-              if (spill_list) {
-                const int r = sset_try_insert(sset, slog, slot);
-                count_it = (r == 1);
-                if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
-              } else {
-                count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
-              }
-            }
-            if (count_it) {
-              ++my_regs;
-              register_slot(a, slot);
-            }
+            s_run_base[tid] = base;
+            s_run_cnt[tid] = 0;
           }
+          __syncthreads();
+        }
+        // phase B: probe, count, dedupe the queued windows
+        for (uint32_t qi = tid; qi < qn; qi += nthr) {
+          const uint32_t w = queue[qi];
+          const uint64_t prefix = tile_key<SB>(tile, sym_off + w, j - 1);
+          const uint32_t last = tile_sym<SB>(tile, sym_off + w + j - 1);
+          uint32_t id = kEmpty32;
+          if (H) {
+            const uint32_t h = hash64_top(prefix, a.hot_log2);
+            if (hot_keys[h] == prefix) id = hot_ids[h];
+          }
+          if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
+          if (id == kEmpty32) continue;
+          const uint32_t slot = (id << SB) | last;
+          if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
           if (a.list_out) {
-            __syncthreads();
-            if (tid == 0) {
-              unsigned long long base = atomicAdd(&a.ctl->list_used, (unsigned long long)s_ccnt);
-              if (base + s_ccnt > a.list_cap) {
-                atomicOr(&a.ctl->status, kStListFull);
-                base = ~0ull;
-              }
-              s_lbase = base;
-              s_lcnt = 0;
-              const uint32_t run = tile_g * a.runs_per_tile + c0 / kRunChunk;
-              a.list_out_off[run] = base;
-              a.list_out_cnt[run] = base == ~0ull ? 0u : s_ccnt;
-            }
-            __syncthreads();
-            if (s_lbase != ~0ull) {
-              for (uint32_t qi = c0 + tid; qi < ce; qi += nthr) {
-                const uint32_t slot = res[qi - c0];
-                if (slot != kEmpty32)
-                  a.list_out[s_lbase + atomicAdd(&s_lcnt, 1u)] =
-                      ((unsigned long long)slot << 32) | (uint32_t)(w0 + queue[qi]);
-              }
+            const uint32_t r = qi / kRunChunk;
+            if (s_run_base[r] != ~0ull)
+              a.list_out[s_run_base[r] + atomicAdd(s_run_cnt + r, 1u)] =
+                  ((unsigned long long)slot << 32) | (uint32_t)(w0 + w);
+          }
+          ++my_surv;
+          bool count_it = true;
+          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+            if (spill_list) {
+              const int r = sset_try_insert(sset, slog, slot);
+              count_it = (r == 1);
+              if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+            } else {
+              count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
             }
           }
+          if (count_it) {
+            ++my_regs;
+            register_slot(a, slot);
+          }
+        }
+        if (a.list_out) {
           __syncthreads();
+          if (tid < nruns) {
+            const uint32_t run = tile_g * a.runs_per_tile + tid;
+            a.list_out_off[run] = s_run_base[tid];
+            a.list_out_cnt[run] = s_run_base[tid] == ~0ull ? 0u : s_run_cnt[tid];
+          }
         }
         if (a.alive_out) {
           __syncthreads();
@@ -540,12 +536,13 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
 template <int SB>
 __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_item, s_nspill, s_lcnt, s_ccnt;
-  __shared__ unsigned long long s_lbase, s_surv, s_regs;
+  __shared__ uint32_t s_item, s_nspill;
+  __shared__ unsigned long long s_surv, s_regs;
+  __shared__ unsigned long long s_run_off[kMaxRuns], s_run_base[kMaxRuns];
+  __shared__ uint32_t s_run_in[kMaxRuns], s_run_cnt[kMaxRuns];
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
   uint32_t* sset = smem;
   uint32_t* scratch = smem + (1u << a.sset_log2);
-  uint32_t* res = scratch;  // kRunChunk results of the current run (free during the spill dedupe)
   uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
   uint32_t* spill_part = spill_list ? spill_list + a.spill_cap : nullptr;
   const uint32_t j = a.j, T = a.tile_windows;
@@ -575,17 +572,33 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
     const uint32_t ntiles = (uint32_t)((W + 1 + T - 1) / T);   // tiles of pass j-1 (W + 1 windows)
     __syncthreads();
     for (uint32_t t = 0; t < ntiles; ++t) {
+      // the tile's input runs, and (if a list is written) output run r
+      // reserved with room for every entry of input run r
+      const uint32_t run0 = (g0 + t) * a.runs_per_tile;
+      if (tid < a.runs_per_tile) {
+        const uint32_t c = a.list_in_cnt[run0 + tid];
+        s_run_in[tid] = c;
+        s_run_off[tid] = a.list_in_off[run0 + tid];
+        if (a.list_out) {
+          unsigned long long base = ~0ull;
+          if (c) {
+            base = atomicAdd(&a.ctl->list_used, (unsigned long long)c);
+            if (base + c > a.list_cap) {
+              atomicOr(&a.ctl->status, kStListFull);
+              base = ~0ull;
+            }
+          }
+          s_run_base[tid] = base;
+          s_run_cnt[tid] = 0;
+        }
+      }
+      __syncthreads();
       for (uint32_t r = 0; r < a.runs_per_tile; ++r) {
-        const uint32_t run = (g0 + t) * a.runs_per_tile + r;
-        const uint32_t n_in = a.list_in_cnt[run];
-        if (n_in == 0) continue;  // uniform across the CTA
-        const unsigned long long off_in = a.list_in_off[run];
-        if (tid == 0) s_ccnt = 0;
-        __syncthreads();
+        const uint32_t n_in = s_run_in[r];
+        const unsigned long long off_in = s_run_off[r];
         for (uint32_t e = tid; e < n_in; e += nthr) {
           const unsigned long long ent = a.list_in[off_in + e];
           const uint32_t w = (uint32_t)ent;
-          res[e] = kEmpty32;
           if (w >= W) continue;  // the last window of pass j-1 has no j-gram
           const uint64_t pos = s0 + w + j - 1;
           uint32_t sym;
@@ -597,9 +610,9 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
           const uint32_t id = probe_table(a.table, a.table_log2, ent >> 32, a.ctl);
           if (id == kEmpty32) continue;
           const uint32_t slot = (id << SB) | sym;
-          res[e] = slot;
-          atomicAdd(&s_ccnt, 1u);
           ++my_surv;
+          if (a.list_out && s_run_base[r] != ~0ull)
+            a.list_out[s_run_base[r] + atomicAdd(s_run_cnt + r, 1u)] = ((unsigned long long)slot << 32) | w;
           bool count_it = true;
           if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
             const int rr = sset_try_insert(sset, slog, slot);
@@ -611,31 +624,11 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
             register_slot(a, slot);
           }
         }
-        if (a.list_out) {
-          // this run's survivors form run r of tile g in the next list
-          __syncthreads();
-          if (tid == 0) {
-            unsigned long long base = atomicAdd(&a.ctl->list_used, (unsigned long long)s_ccnt);
-            if (base + s_ccnt > a.list_cap) {
-              atomicOr(&a.ctl->status, kStListFull);
-              base = ~0ull;
-            }
-            s_lbase = base;
-            s_lcnt = 0;
-            a.list_out_off[run] = base;
-            a.list_out_cnt[run] = base == ~0ull ? 0u : s_ccnt;
-          }
-          __syncthreads();
-          if (s_lbase != ~0ull) {
-            for (uint32_t e = tid; e < n_in; e += nthr) {
-              const uint32_t slot = res[e];
-              if (slot != kEmpty32)
-                a.list_out[s_lbase + atomicAdd(&s_lcnt, 1u)] =
-                    ((unsigned long long)slot << 32) | (uint32_t)a.list_in[off_in + e];
-            }
-          }
-        }
-        __syncthreads();
+      }
+      __syncthreads();
+      if (a.list_out && tid < a.runs_per_tile) {
+        a.list_out_off[run0 + tid] = s_run_base[tid];
+        a.list_out_cnt[run0 + tid] = s_run_base[tid] == ~0ull ? 0u : s_run_cnt[tid];
       }
     }
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {

@@ -281,3 +281,24 @@ def test_repeatable():
     a = O.intergrams(data, off, 6, 50, 64, base_n=2)
     b = O.intergrams(data, off, 6, 50, 64, base_n=2)
     assert a[0].tolist() == b[0].tolist() and a[1].tolist() == b[1].tolist()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("bits", [8, 2])
+def test_count_keys_matches_exhaustive(mode, bits):
+    """Exact counts of chosen n-grams agree with the exhaustive count (and
+    absent keys count zero)."""
+    rng = np.random.default_rng(40 + mode + bits)
+    sigma = 4 if bits == 2 else 6
+    seqs = random_seqs(rng, 7, 300, sigma)
+    flat = [c for s in seqs for c in s]
+    data = _pack_by_hand(flat) if bits == 2 else np.asarray(flat, np.uint8)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([len(s) for s in seqs])
+    for n in (1, 3, 9):
+        ek, ec = O.exhaustive(data, off, n, 10 ** 6, mode, symbol_bits=bits)
+        pick = rng.choice(len(ek), size=min(25, len(ek)), replace=False)
+        keys = np.concatenate([ek[pick], np.full((1, n), sigma - 1 if n > 3 else 0, np.uint8)])
+        got = O.count_keys(data, off, keys, mode, symbol_bits=bits)
+        table = {bytes(k): int(c) for k, c in zip(ek, ec)}
+        assert got.tolist() == [table.get(bytes(k), 0) for k in keys]
