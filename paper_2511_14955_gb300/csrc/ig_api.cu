@@ -118,6 +118,7 @@ struct ig_plan {
   cudaGraphExec_t graph = nullptr;  // full job from the first pass (IG_F_GRAPH)
   cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
   bool check_overflow = false;
+  bool narrow = false;               // 16-bit counters (every count provably < 65536)
 };
 
 namespace {
@@ -199,7 +200,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   const bool seq_mode = pl->p.count_mode == IG_COUNT_ONCE_PER_SEQUENCE;
   launch_pass_reset(pl->ctl, pl->m, nullptr, 0, s);
   kernels += 1;
-  cudaMemsetAsync(pl->counts, 0, ns * sizeof(uint32_t), s);
+  cudaMemsetAsync(pl->counts, 0, pl->narrow ? ((ns + 1) / 2) * sizeof(uint32_t) : ns * sizeof(uint32_t), s);
   ScanArgs a{};
   a.data = pl->data;
   a.data_bytes = pl->data_bytes;
@@ -222,6 +223,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.tile_words = pl->tile_words;
   a.queue_words = pl->queue_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
+  a.narrow = pl->narrow ? 1u : 0u;
   a.tile_base = pl->d_tile_base;
   a.tile_windows = pl->tile_windows;
   a.runs_per_tile = pl->runs_per_tile;
@@ -255,8 +257,8 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   const uint32_t target = (j < pl->p.n) ? pl->p.candidates : pl->p.k;
   // the scan of a candidate pass counted in rank space; selection reads the
   // counters back in byte order through the rank map
-  launch_select(pl->counts, base ? nullptr : pl->rank, pl->sb, ns, target, pl->ctl, pl->hist, pl->blk, pl->G,
-                sel, pl->sel_count, s);
+  launch_select(pl->counts, pl->narrow, base ? nullptr : pl->rank, pl->sb, ns, target, pl->ctl, pl->hist, pl->blk,
+                pl->G, sel, pl->sel_count, s);
   kernels += 12;
   if (j < pl->p.n) {
     const int nxt = pl->cur ^ 1;
@@ -489,6 +491,10 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
 
   // Eq. 1 with 2^32 or more windows can overflow a 32-bit count
   pl->check_overflow = p->count_mode == IG_COUNT_EVERY_OCCURRENCE && pl->total_syms >= 0xFFFFFFFFull;
+  // 16-bit counters when no count can reach 65536: Eq. 2 counts are at most m,
+  // Eq. 1 counts at most the number of windows (halves the counter array, so
+  // far more of it stays in L2)
+  pl->narrow = (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE) ? (m < 65536u) : (pl->total_syms < 65536u);
 
   // scan launch geometry: shared memory = dedupe set + hot cache + tile (with
   // halo and alignment slop) + candidate queue (2 bytes per tile window) +
@@ -543,7 +549,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   }
   pl->ntiles = tile_base[m];
 
-  PLAN_CUDA(dev_alloc(pl, &pl->counts, nslots));
+  PLAN_CUDA(dev_alloc(pl, &pl->counts, pl->narrow ? (nslots + 1) / 2 : nslots));
   pl->alive_words = (pl->total_syms + 31) / 32 + 1;
   if (p->n >= pl->b + 2) {
     PLAN_CUDA(dev_alloc(pl, &pl->alive[0], pl->alive_words));

@@ -77,6 +77,7 @@ struct ScanArgs {
   uint32_t tile_words;         // 32-bit words in the shared-memory tile buffer
   uint32_t queue_words;        // 32-bit words of the candidate queue (2 bytes per tile window) + survivor bits
   uint32_t check_overflow;     // Eq. 1 with >= 2^32 windows: detect count wrap
+  uint32_t narrow;             // 16-bit counters (two per word): every count is known to be < 65536
   // survivor bitmasks (bit p: the window starting at corpus symbol p survived)
   const uint32_t* alive_in;    // previous pass's survivors; null = every window is a candidate
   uint32_t* alive_out;         // this pass's survivors; null = not needed
@@ -114,9 +115,10 @@ cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t s
 void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint64_t gset_entries, cudaStream_t s);
 // rank: null for the dense base pass; otherwise the counter of slot id*sigma+sym is
 // at rank[id]*sigma+sym (candidate passes count in rank space)
-void launch_select(const uint32_t* counts, const uint32_t* rank, uint32_t sb, uint64_t ns, uint32_t target,
-                   PassCtl* ctl, uint32_t* hist /* kMaxLevels*kHistBins */, uint32_t* blk /* 2*G */, int G,
-                   uint32_t* sel_slot, uint32_t* sel_count, cudaStream_t s);
+// narrow: the counters are 16-bit (counter s is the s-th uint16_t)
+void launch_select(const uint32_t* counts, bool narrow, const uint32_t* rank, uint32_t sb, uint64_t ns,
+                   uint32_t target, PassCtl* ctl, uint32_t* hist /* kMaxLevels*kHistBins */,
+                   uint32_t* blk /* 2*G */, int G, uint32_t* sel_slot, uint32_t* sel_count, cudaStream_t s);
 // rank[order[x]] = x for the nsel selected candidates, rank[i] = i beyond
 void launch_rank(const uint32_t* order, const PassCtl* ctl, uint32_t* rank, uint32_t n, cudaStream_t s);
 void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap,

@@ -158,7 +158,7 @@ extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void
   a.check_overflow = (p->count_mode == IG_COUNT_EVERY_OCCURRENCE && total_symbols >= 0xFFFFFFFFull) ? 1u : 0u;
   a.ctl = ctl;
   if (m) launch_scan(a, sb, true, (int)kGrid, (int)kThreads, smem, s);
-  launch_select(counts, nullptr, sb, nslots, p->k, ctl, reinterpret_cast<uint32_t*>(S + L.hist),
+  launch_select(counts, false, nullptr, sb, nslots, p->k, ctl, reinterpret_cast<uint32_t*>(S + L.hist),
                 reinterpret_cast<uint32_t*>(S + L.blk), 1024, reinterpret_cast<uint32_t*>(S + L.sel_slot),
                 reinterpret_cast<uint32_t*>(S + L.sel_count), s);
   launch_sort_by_count(reinterpret_cast<uint32_t*>(S + L.sel_count), ctl, kMaxSlots,

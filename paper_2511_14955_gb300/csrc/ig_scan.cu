@@ -164,6 +164,10 @@ __device__ __forceinline__ uint32_t spill_bucket(uint32_t x, uint32_t shift, uin
 }
 
 __device__ __forceinline__ void register_slot(const ScanArgs& a, uint32_t slot) {
+  if (a.narrow) {  // 16-bit counter slot of word slot / 2 (little-endian half); counts < 65536
+    atomicAdd(a.counts + (slot >> 1), 1u << ((slot & 1u) << 4));
+    return;
+  }
   if (a.check_overflow) {
     if (atomicAdd(a.counts + slot, 1u) == 0xFFFFFFFFu) atomicOr(&a.ctl->status, kStCountOverflow);
   } else {

@@ -71,10 +71,14 @@ __global__ void sel_reset_kernel(PassCtl* ctl, uint32_t target, uint32_t* hist) 
   }
 }
 
-__global__ void max_nonzero_kernel(const uint32_t* __restrict__ c, uint64_t ns, PassCtl* ctl) {
+__device__ __forceinline__ uint32_t load_counter(const uint32_t* __restrict__ c, bool narrow, uint64_t i) {
+  return narrow ? (uint32_t)reinterpret_cast<const uint16_t*>(c)[i] : c[i];
+}
+
+__global__ void max_nonzero_kernel(const uint32_t* __restrict__ c, bool narrow, uint64_t ns, PassCtl* ctl) {
   uint32_t mx = 0, nz = 0;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < ns; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t v = c[i];
+    uint32_t v = load_counter(c, narrow, i);
     mx = v > mx ? v : mx;
     nz += v != 0;
   }
@@ -110,14 +114,15 @@ __device__ __forceinline__ uint32_t level_shift(uint32_t lo, uint32_t hi) {
   return l > 12 ? l - 12 : 0;
 }
 
-__global__ void level_hist_kernel(const uint32_t* __restrict__ c, uint64_t ns, PassCtl* ctl, uint32_t* hist) {
+__global__ void level_hist_kernel(const uint32_t* __restrict__ c, bool narrow, uint64_t ns, PassCtl* ctl,
+                                  uint32_t* hist) {
   __shared__ uint32_t sh[kHistBins];
   if (ctl->done) return;
   const uint32_t lo = ctl->lo, hi = ctl->hi, sh_bits = level_shift(lo, hi);
   for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < ns; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t v = c[i];
+    uint32_t v = load_counter(c, narrow, i);
     if (v >= lo && v <= hi) atomicAdd(sh + ((v - lo) >> sh_bits), 1u);
   }
   __syncthreads();
@@ -157,21 +162,21 @@ __global__ void level_pick_kernel(PassCtl* ctl, uint32_t* hist) {
 // Stable compaction, phase 1: per-block numbers of counters > thr and == thr.
 // Counter of slot s (byte order). Candidate passes count in rank space:
 // slot id * sigma + sym lives at rank[id] * sigma + sym.
-__device__ __forceinline__ uint32_t counter_of(const uint32_t* __restrict__ c, const uint32_t* __restrict__ rank,
-                                               uint32_t sb, uint64_t s) {
-  if (!rank) return c[s];
+__device__ __forceinline__ uint32_t counter_of(const uint32_t* __restrict__ c, bool narrow,
+                                               const uint32_t* __restrict__ rank, uint32_t sb, uint64_t s) {
+  if (!rank) return load_counter(c, narrow, s);
   const uint64_t id = s >> sb;
-  return c[((uint64_t)rank[id] << sb) | (s & ((1u << sb) - 1u))];
+  return load_counter(c, narrow, ((uint64_t)rank[id] << sb) | (s & ((1u << sb) - 1u)));
 }
 
-__global__ void compact_count_kernel(const uint32_t* __restrict__ c, const uint32_t* __restrict__ rank, uint32_t sb,
-                                     uint64_t ns, const PassCtl* ctl, uint32_t* blk, uint64_t chunk) {
+__global__ void compact_count_kernel(const uint32_t* __restrict__ c, bool narrow, const uint32_t* __restrict__ rank,
+                                     uint32_t sb, uint64_t ns, const PassCtl* ctl, uint32_t* blk, uint64_t chunk) {
   const uint32_t thr = ctl->thr;
   const bool eq_used = !ctl->take_all;
   const uint64_t b0 = blockIdx.x * chunk, b1 = min(ns, b0 + chunk);
   uint32_t gt = 0, eq = 0;
   for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    uint32_t v = counter_of(c, rank, sb, i);
+    uint32_t v = counter_of(c, narrow, rank, sb, i);
     gt += v > thr;
     eq += eq_used && v == thr;
   }
@@ -245,8 +250,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_t
 }
 
 // Phase 3: write the selected (slot, count) pairs in slot order.
-__global__ void compact_write_kernel(const uint32_t* __restrict__ c, const uint32_t* __restrict__ rank, uint32_t sb,
-                                     uint64_t ns, const PassCtl* ctl, const uint32_t* blk, uint64_t chunk,
+__global__ void compact_write_kernel(const uint32_t* __restrict__ c, bool narrow, const uint32_t* __restrict__ rank,
+                                     uint32_t sb, uint64_t ns, const PassCtl* ctl, const uint32_t* blk, uint64_t chunk,
                                      uint32_t* sel_slot, uint32_t* sel_count) {
   __shared__ uint32_t wt[33];
   const uint32_t thr = ctl->thr, need = ctl->need_eq;
@@ -255,7 +260,7 @@ __global__ void compact_write_kernel(const uint32_t* __restrict__ c, const uint3
   uint32_t base_gt = blk[2 * blockIdx.x], base_eq = blk[2 * blockIdx.x + 1];
   for (uint64_t t0 = b0; t0 < b1; t0 += blockDim.x) {
     uint64_t i = t0 + threadIdx.x;
-    uint32_t v = i < b1 ? counter_of(c, rank, sb, i) : 0u;
+    uint32_t v = i < b1 ? counter_of(c, narrow, rank, sb, i) : 0u;
     uint32_t gt = v > thr, eq = eq_used && i < b1 && v == thr;
     uint32_t tg, te;
     uint32_t rg = block_excl_scan(gt, wt, tg);
@@ -366,23 +371,24 @@ void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint6
   }
 }
 
-void launch_select(const uint32_t* counts, const uint32_t* rank, uint32_t sb, uint64_t ns, uint32_t target,
-                   PassCtl* ctl, uint32_t* hist, uint32_t* blk, int G, uint32_t* sel_slot, uint32_t* sel_count,
-                   cudaStream_t s) {
+void launch_select(const uint32_t* counts, bool narrow, const uint32_t* rank, uint32_t sb, uint64_t ns,
+                   uint32_t target, PassCtl* ctl, uint32_t* hist, uint32_t* blk, int G, uint32_t* sel_slot,
+                   uint32_t* sel_count, cudaStream_t s) {
   sel_reset_kernel<<<1, 1024, 0, s>>>(ctl, target, hist);
   int grid = 4 * 152;
-  max_nonzero_kernel<<<grid, kThreads, 0, s>>>(counts, ns, ctl);
+  max_nonzero_kernel<<<grid, kThreads, 0, s>>>(counts, narrow, ns, ctl);
   threshold_init_kernel<<<1, 32, 0, s>>>(ctl);
   for (int l = 0; l < 3; ++l) {
-    level_hist_kernel<<<grid, 512, 0, s>>>(counts, ns, ctl, hist);
+    level_hist_kernel<<<grid, 512, 0, s>>>(counts, narrow, ns, ctl, hist);
     level_pick_kernel<<<1, 32, 0, s>>>(ctl, hist);
   }
   uint64_t chunk = (ns + G - 1) / G;
   chunk = (chunk + 255) & ~255ull;
   if (chunk == 0) chunk = 256;
-  compact_count_kernel<<<G, kThreads, 0, s>>>(counts, rank, sb, ns, ctl, blk, chunk);
+  compact_count_kernel<<<G, kThreads, 0, s>>>(counts, narrow, rank, sb, ns, ctl, blk, chunk);
   compact_scan_kernel<<<1, 1024, 0, s>>>(blk, G);
-  compact_write_kernel<<<G, kThreads, 0, s>>>(counts, rank, sb, ns, ctl, blk, chunk, sel_slot, sel_count);
+  compact_write_kernel<<<G, kThreads, 0, s>>>(counts, narrow, rank, sb, ns, ctl, blk, chunk, sel_slot,
+                                             sel_count);
 }
 
 void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap, uint32_t* idx_a,

@@ -163,6 +163,18 @@ def test_edge_cases():
             check_all_passes(data, off, n=3, k=3, Z=3, base_n=3, mode=mode)   # n == base_n
 
 
+def test_many_short_sequences_use_32bit_counters():
+    """m >= 65536 sequences: Eq. 2 counts may exceed 16 bits, so the counters are 32-bit."""
+    rng = np.random.default_rng(17)
+    m = 70000
+    lens = rng.integers(3, 24, size=m)
+    off = np.zeros(m + 1, np.uint64)
+    off[1:] = np.cumsum(lens)
+    # a small alphabet so that counts go far beyond 65535 for the top n-grams
+    data = rng.integers(0, 3, size=int(off[-1])).astype(np.uint8)
+    check_all_passes(data, off, n=5, k=40, Z=150, base_n=2)
+
+
 def test_k_equals_candidates_and_single_candidate():
     data, off, _ = synth.make_corpus("markov_2mb", m=8, seed=5)
     check_all_passes(data, off, n=6, k=64, Z=64, base_n=1)
