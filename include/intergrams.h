@@ -91,6 +91,17 @@ typedef struct {
   uint32_t list_pct;         /* capacity of each survivor list, percent of the corpus symbols
                                 (default: 100 when two full lists fit in 25% of the free device
                                 memory, else 25; exceeding it returns IG_ETABLE_FULL) */
+  /* Registration log of the candidate passes: a count increment is appended to
+     a log chunk of its counter range and the log is counted range by range
+     after the scan, so the increments of any moment fall in one range of the
+     counter array (results are identical; only speed and memory change). */
+  uint32_t log_mode;         /* 0 = off (default), 1 = on */
+  uint32_t log_pct;          /* log capacity in percent of the corpus symbols (default 60 under Eq. 2,
+                                80 under Eq. 1, plus the chunks held open; at most a quarter of the
+                                device memory). Registrations past it are counted at once */
+  uint32_t log_chunk_log2;   /* log2 entries of a log chunk (14..20; default 18) */
+  uint32_t log_range_log2;   /* log2 counters of one range (10..30; default 16 MiB of counters);
+                                raised until there are at most 32 ranges */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -19,6 +19,11 @@ constexpr int kSortDigits = 256;     // 8-bit digits of the final stable sort
 constexpr int kSortChunk = 1024;     // elements per one-warp block of the stable sort
 constexpr uint32_t kRunChunk = 2048; // survivors are listed in runs of at most this many candidates
 constexpr uint32_t kMaxRuns = 64;    // runs per tile (tile windows <= 65536 / ... / kRunChunk)
+// registration log: a CTA holds one open chunk per counter range and, before
+// a step that registers at most chunk / 8 slots, makes room for that many in
+// each
+constexpr uint32_t kLogMaxRanges = 32;
+constexpr uint32_t kNoChunk = 0xFFFFFFFEu;  // range has no open chunk yet (kEmpty32: pool exhausted)
 
 // Sticky device status bits (PassCtl::status).
 enum : uint32_t {
@@ -51,7 +56,7 @@ struct PassCtl {
   uint32_t epoch_base;
   uint32_t epoch_next;
   uint32_t gset_clear;               // epochs wrapped: clear the dedupe sets before the scan
-  uint32_t pad;
+  uint32_t rlog_next;                // registration-log chunks handed out in this pass
   unsigned long long list_used;      // entries reserved in this pass's survivor list
 };
 
@@ -97,6 +102,17 @@ struct ScanArgs {
   uint32_t* list_out_cnt;
   unsigned long long list_cap;
   uint32_t runs_per_tile;
+  // registration log (counter arrays far larger than L2): a registered slot is
+  // appended to the CTA's open chunk for its counter range (slot >> range_shift)
+  // and counted later, one range at a time, by launch_log_count; null = count
+  // at once. A CTA that finds the pool exhausted counts at once.
+  uint32_t* rlog;              // rlog_chunks chunks of 2^rlog_chunk_log2 slots
+  uint32_t* rlog_range;        // counter range of each handed-out chunk
+  uint32_t* rlog_fill;         // slots in each handed-out chunk
+  uint32_t rlog_chunks;
+  uint32_t rlog_chunk_log2;
+  uint32_t range_shift;
+  uint32_t nranges;            // <= kLogMaxRanges
   PassCtl* ctl;
 };
 
@@ -110,6 +126,9 @@ cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t sme
 cudaError_t chain_set_smem_limit(uint32_t symbol_bits, size_t smem);
 // Raise (never lower) the scan kernel's dynamic shared-memory limit to `smem`.
 cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem);
+// Count the registration log of the pass just scanned: one launch per counter
+// range, so the counters being incremented at any time span one range.
+void launch_log_count(const ScanArgs& a, cudaStream_t s);
 
 // Launchers (ig_select.cu)
 void launch_pass_reset(PassCtl* ctl, uint32_t m, unsigned long long* gset, uint64_t gset_entries, cudaStream_t s);

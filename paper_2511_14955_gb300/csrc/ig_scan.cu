@@ -163,7 +163,7 @@ __device__ __forceinline__ uint32_t spill_bucket(uint32_t x, uint32_t shift, uin
   return kb == 0 ? 0u : (x << shift) >> (32 - kb);
 }
 
-__device__ __forceinline__ void register_slot(const ScanArgs& a, uint32_t slot) {
+__device__ __forceinline__ void count_at_once(const ScanArgs& a, uint32_t slot) {
   if (a.narrow) {  // 16-bit counter slot of word slot / 2 (little-endian half); counts < 65536
     atomicAdd(a.counts + (slot >> 1), 1u << ((slot & 1u) << 4));
     return;
@@ -175,18 +175,88 @@ __device__ __forceinline__ void register_slot(const ScanArgs& a, uint32_t slot) 
   }
 }
 
+// The CTA's registration-log state in shared memory: open chunk and fill of
+// each counter range.
+struct LogState {
+  uint32_t* chunk;
+  uint32_t* fill;
+};
+
+__device__ __forceinline__ void log_init(const LogState& lg) {
+  if (threadIdx.x < kLogMaxRanges) {
+    lg.chunk[threadIdx.x] = kNoChunk;
+    lg.fill[threadIdx.x] = 0;
+  }
+}
+
+// Count `slot` (Eq. 1 / Eq. 2 increment of C): appended to the log when the
+// pass keeps one, else counted at once. A chunk that is somehow full also
+// falls back to counting at once, so the log never overflows.
+__device__ __forceinline__ void register_slot(const ScanArgs& a, const LogState& lg, uint32_t slot) {
+  if (a.rlog) {
+    const uint32_t r = slot >> a.range_shift;
+    const uint32_t c = lg.chunk[r];
+    if (c < kNoChunk) {
+      // one shared-memory atomic per range among the lanes registering now
+      const uint32_t peers = __match_any_sync(__activemask(), r);
+      const uint32_t lane = threadIdx.x & 31u, leader = __ffs(peers) - 1;
+      uint32_t pos = 0;
+      if (lane == leader) pos = atomicAdd(lg.fill + r, (uint32_t)__popc(peers));
+      pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+      if (pos < (1u << a.rlog_chunk_log2)) {
+        a.rlog[((uint64_t)c << a.rlog_chunk_log2) + pos] = slot;
+        return;
+      }
+    }
+  }
+  count_at_once(a, slot);
+}
+
+// Before a step that registers at most `need` slots (threads < nranges; the
+// caller synchronises before the step and after it): every range's open
+// chunk gets room for `need` more entries; a chunk without room is closed and
+// a new one taken from the pool.
+__device__ __forceinline__ void log_room(const ScanArgs& a, const LogState& lg, uint32_t need) {
+  const uint32_t r = threadIdx.x;
+  if (!a.rlog || r >= a.nranges) return;
+  const uint32_t size = 1u << a.rlog_chunk_log2;
+  uint32_t c = lg.chunk[r];
+  if (c == kEmpty32) return;  // pool exhausted: this CTA counts at once
+  if (c != kNoChunk) {
+    if (lg.fill[r] + need <= size) return;
+    a.rlog_fill[c] = lg.fill[r] < size ? lg.fill[r] : size;
+  }
+  c = atomicAdd(&a.ctl->rlog_next, 1u);
+  if (c < a.rlog_chunks) {
+    a.rlog_range[c] = r;
+    lg.chunk[r] = c;
+  } else {
+    lg.chunk[r] = kEmpty32;
+  }
+  lg.fill[r] = 0;
+}
+
+// Kernel end (after a barrier): close the open chunks.
+__device__ __forceinline__ void log_close(const ScanArgs& a, const LogState& lg) {
+  const uint32_t r = threadIdx.x;
+  if (!a.rlog || r >= a.nranges) return;
+  const uint32_t c = lg.chunk[r], size = 1u << a.rlog_chunk_log2;
+  if (c < kNoChunk) a.rlog_fill[c] = lg.fill[r] < size ? lg.fill[r] : size;
+}
+
 // Exact dedupe of src[lo, hi) in the (cleared) shared-memory set; each
 // distinct slot is registered once. Fits whenever hi - lo <= capacity / 2.
-__device__ void insert_range(const ScanArgs& a, const uint32_t* src, uint32_t lo, uint32_t hi, uint32_t* sset,
-                             unsigned long long& my_regs) {
+__device__ void insert_range(const ScanArgs& a, const LogState& lg, const uint32_t* src, uint32_t lo, uint32_t hi,
+                             uint32_t* sset, unsigned long long& my_regs) {
   const uint32_t tid = threadIdx.x, nthr = blockDim.x, cap = 1u << a.sset_log2;
   for (uint32_t i = tid; i < cap; i += nthr) sset[i] = kEmpty32;
+  log_room(a, lg, hi - lo);
   __syncthreads();
   for (uint32_t i = lo + tid; i < hi; i += nthr) {
     const uint32_t v = src[i];
     if (sset_insert_full(sset, a.sset_log2, v, a.ctl)) {
       ++my_regs;
-      register_slot(a, v);
+      register_slot(a, lg, v);
     }
   }
   __syncthreads();
@@ -225,12 +295,12 @@ __device__ __forceinline__ uint32_t bucket_bits(uint32_t n, uint32_t cap, uint32
 // included, disjoint from the slots already in the set) are hash-partitioned
 // (at most two levels, bucket tables in the free tile buffer) into buckets of
 // at most half the set's capacity, and each bucket is deduplicated exactly.
-__device__ void dedupe_spills(const ScanArgs& a, uint32_t S, uint32_t* sset, uint32_t* scratch,
+__device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t* sset, uint32_t* scratch,
                               uint32_t scratch_words, uint32_t* list, uint32_t* part,
                               unsigned long long& my_regs) {
   const uint32_t cap = 1u << a.sset_log2, fit = cap / 2;
   if (S <= fit) {
-    insert_range(a, list, 0, S, sset, my_regs);
+    insert_range(a, lg, list, 0, S, sset, my_regs);
     return;
   }
   const uint32_t half = scratch_words / 2;
@@ -246,7 +316,7 @@ __device__ void dedupe_spills(const ScanArgs& a, uint32_t S, uint32_t* sset, uin
     const uint32_t lo = bnd1[b1], hi = bnd1[b1 + 1];
     if (hi == lo) continue;  // uniform across the CTA
     if (hi - lo <= fit) {
-      insert_range(a, part, lo, hi, sset, my_regs);
+      insert_range(a, lg, part, lo, hi, sset, my_regs);
       continue;
     }
     const uint32_t kb2 = bucket_bits(hi - lo, cap, kbmax);
@@ -254,7 +324,7 @@ __device__ void dedupe_spills(const ScanArgs& a, uint32_t S, uint32_t* sset, uin
     partition_range(part, list, lo, hi, kb1, kb2, bnd2, bnd2 + K2 + 1);
     for (uint32_t b2 = 0; b2 < K2; ++b2) {
       const uint32_t l2 = bnd2[b2], h2 = bnd2[b2 + 1];
-      if (h2 > l2) insert_range(a, list, l2, h2, sset, my_regs);
+      if (h2 > l2) insert_range(a, lg, list, l2, h2, sset, my_regs);
     }
   }
 }
@@ -266,6 +336,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   __shared__ unsigned long long s_run_base[kMaxRuns];
   __shared__ uint32_t s_run_cnt[kMaxRuns];
   __shared__ unsigned long long s_surv, s_regs;
+  __shared__ uint32_t s_log_chunk[kLogMaxRanges], s_log_fill[kLogMaxRanges];
+  const LogState lg{s_log_chunk, s_log_fill};
+  log_init(lg);
 
   using S = Sym<SB>;
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
@@ -388,7 +461,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             }
             if (count_it) {
               ++my_regs;
-              register_slot(a, slot);
+              count_at_once(a, slot);  // the dense base pass never keeps a log
             }
           }
         }
@@ -448,8 +521,16 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           }
           __syncthreads();
         }
-        // phase B: probe, count, dedupe the queued windows
-        for (uint32_t qi = tid; qi < qn; qi += nthr) {
+        // phase B: probe, count, dedupe the queued windows (in steps of at
+        // most chunk / 8 when registrations go to the log)
+        const uint32_t step = a.rlog ? (1u << a.rlog_chunk_log2) >> 3 : (qn ? qn : 1u);
+        for (uint32_t q0 = 0; q0 < qn; q0 += step) {
+        const uint32_t q1 = qn - q0 < step ? qn : q0 + step;
+        if (a.rlog) {
+          log_room(a, lg, q1 - q0);
+          __syncthreads();
+        }
+        for (uint32_t qi = q0 + tid; qi < q1; qi += nthr) {
           const uint32_t w = queue[qi];
           const uint64_t prefix = tile_key<SB>(tile, sym_off + w, j - 1);
           const uint32_t last = tile_sym<SB>(tile, sym_off + w + j - 1);
@@ -481,8 +562,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           }
           if (count_it) {
             ++my_regs;
-            register_slot(a, slot);
+            register_slot(a, lg, slot);
           }
+        }
+        if (a.rlog) __syncthreads();
         }
         if (a.list_out) {
           __syncthreads();
@@ -510,7 +593,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     }
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       const uint32_t nsp = s_nspill;  // read after the tile loop's final barrier
-      if (nsp) dedupe_spills(a, nsp, sset, tile, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
+      if (nsp) dedupe_spills(a, lg, nsp, sset, tile, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
       __syncthreads();
     }
   }
@@ -524,6 +607,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     atomicAdd(&s_regs, my_regs);
   }
   __syncthreads();
+  log_close(a, lg);
   if (tid == 0) {
     atomicAdd(&a.ctl->survivors, s_surv);
     atomicAdd(&a.ctl->registrations, s_regs);
@@ -544,6 +628,9 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
   __shared__ unsigned long long s_surv, s_regs;
   __shared__ unsigned long long s_run_off[kMaxRuns], s_run_base[kMaxRuns];
   __shared__ uint32_t s_run_in[kMaxRuns], s_run_cnt[kMaxRuns];
+  __shared__ uint32_t s_log_chunk[kLogMaxRanges], s_log_fill[kLogMaxRanges];
+  const LogState lg{s_log_chunk, s_log_fill};
+  log_init(lg);
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
   uint32_t* sset = smem;
   uint32_t* scratch = smem + (1u << a.sset_log2);
@@ -597,7 +684,15 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
         }
       }
       __syncthreads();
-      for (uint32_t r = 0; r < a.runs_per_tile; ++r) {
+      // runs in groups of at most chunk / 8 entries when registrations go to the log
+      const uint32_t group = a.rlog ? ((1u << a.rlog_chunk_log2) >> 3) / kRunChunk : a.runs_per_tile;
+      for (uint32_t r0 = 0; r0 < a.runs_per_tile; r0 += group) {
+      const uint32_t r1 = a.runs_per_tile - r0 < group ? a.runs_per_tile : r0 + group;
+      if (a.rlog) {
+        log_room(a, lg, (r1 - r0) * kRunChunk);
+        __syncthreads();
+      }
+      for (uint32_t r = r0; r < r1; ++r) {
         const uint32_t n_in = s_run_in[r];
         const unsigned long long off_in = s_run_off[r];
         for (uint32_t e = tid; e < n_in; e += nthr) {
@@ -625,9 +720,11 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
           }
           if (count_it) {
             ++my_regs;
-            register_slot(a, slot);
+            register_slot(a, lg, slot);
           }
         }
+      }
+      if (a.rlog) __syncthreads();
       }
       __syncthreads();
       if (a.list_out && tid < a.runs_per_tile) {
@@ -638,7 +735,7 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       __syncthreads();
       const uint32_t nsp = s_nspill;
-      if (nsp) dedupe_spills(a, nsp, sset, scratch, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
+      if (nsp) dedupe_spills(a, lg, nsp, sset, scratch, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
     }
     __syncthreads();
   }
@@ -651,9 +748,30 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
     atomicAdd(&s_regs, my_regs);
   }
   __syncthreads();
+  log_close(a, lg);
   if (tid == 0) {
     atomicAdd(&a.ctl->survivors, s_surv);
     atomicAdd(&a.ctl->registrations, s_regs);
+  }
+}
+
+// Counting of the registration log, range r: each block takes whole chunks
+// of that range and increments their slots' counters (16-byte loads; chunks
+// are at least 64 KiB and the pool is 256-byte aligned).
+__global__ void __launch_bounds__(512) log_count_kernel(const ScanArgs a, uint32_t r) {
+  const uint32_t used = a.ctl->rlog_next < a.rlog_chunks ? a.ctl->rlog_next : a.rlog_chunks;
+  for (uint32_t c = blockIdx.x; c < used; c += gridDim.x) {
+    if (a.rlog_range[c] != r) continue;  // uniform across the block
+    const uint32_t n = a.rlog_fill[c];
+    const uint4* e = reinterpret_cast<const uint4*>(a.rlog + ((uint64_t)c << a.rlog_chunk_log2));
+    for (uint32_t i = threadIdx.x; 4 * i < n; i += blockDim.x) {
+      const uint4 v = __ldcs(e + i);
+      const uint32_t b = 4 * i;
+      count_at_once(a, v.x);
+      if (b + 1 < n) count_at_once(a, v.y);
+      if (b + 2 < n) count_at_once(a, v.z);
+      if (b + 3 < n) count_at_once(a, v.w);
+    }
   }
 }
 
@@ -698,6 +816,10 @@ int scan_max_ctas_per_sm(uint32_t symbol_bits, bool base_pass, int threads, size
       cudaSuccess)
     return 0;
   return n;
+}
+
+void launch_log_count(const ScanArgs& a, cudaStream_t s) {
+  for (uint32_t r = 0; r < a.nranges; ++r) log_count_kernel<<<8 * 152, 512, 0, s>>>(a, r);
 }
 
 void launch_scan(const ScanArgs& a, uint32_t symbol_bits, bool base_pass, int grid, int threads,

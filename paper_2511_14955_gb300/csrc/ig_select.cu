@@ -34,6 +34,7 @@ __global__ void pass_reset_kernel(PassCtl* ctl, uint32_t m) {
     ctl->survivors = 0;
     ctl->registrations = 0;
     ctl->list_used = 0;
+    ctl->rlog_next = 0;
     uint64_t e = ctl->epoch_next;
     if (e + m + 1 > 0xFFFFFFFFull) {
       ctl->gset_clear = 1;

@@ -163,6 +163,30 @@ def test_edge_cases():
             check_all_passes(data, off, n=3, k=3, Z=3, base_n=3, mode=mode)   # n == base_n
 
 
+# registration log forced on, with small chunks (steps of 2048 registrations)
+# and a 2^19-slot counter array split into 32 ranges
+LOG_ON = dict(log_mode=1, log_chunk_log2=14, log_range_log2=12)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_registration_log_every_pass(mode):
+    """Registrations go to per-range log chunks and are counted range by range after each scan."""
+    data, off, _ = synth.make_corpus("malware_8gb", m=40, max_len=64 * 1024, seed=9)
+    check_all_passes(data, off, n=8, k=512, Z=2048, base_n=3, mode=mode, tuning=LOG_ON)
+
+
+def test_registration_log_pool_exhausted():
+    """A log of one chunk: once the pool is used up, registrations are counted at once."""
+    data, off, _ = synth.make_corpus("malware_8gb", m=40, max_len=64 * 1024, seed=10)
+    check_all_passes(data, off, n=6, k=256, Z=2048, base_n=2, tuning=dict(LOG_ON, log_pct=1))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_registration_log_with_chain_passes(mode):
+    data, off, _ = synth.make_corpus("largen_6gb", m=24, max_len=12000, seed=4)
+    check_passes(data, off, n=16, k=200, Z=800, base_n=3, js={4, 9, 10, 16}, mode=mode, tuning=LOG_ON)
+
+
 def test_many_short_sequences_use_32bit_counters():
     """m >= 65536 sequences: Eq. 2 counts may exceed 16 bits, so the counters are 32-bit."""
     rng = np.random.default_rng(17)
