@@ -102,6 +102,11 @@ typedef struct {
   uint32_t log_chunk_log2;   /* log2 entries of a log chunk (14..20; default 18) */
   uint32_t log_range_log2;   /* log2 counters of one range (10..30; default 16 MiB of counters);
                                 raised until there are at most 32 ranges */
+  uint32_t dedupe_bitmap;    /* Eq. 2 dedupe of a pass by a per-CTA bit vector over its slots (the
+                                paper's C_i, Sec. 6) instead of the shared-memory set with spill
+                                lists: 0 = auto (when the scan CTAs' bit vectors take at most
+                                48 MiB), 1 = never, 2 = whenever they fit in a quarter of the
+                                device memory */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -124,6 +124,9 @@ struct ig_plan {
   uint32_t* rlog_range = nullptr;
   uint32_t* rlog_fill = nullptr;
   uint32_t rlog_chunks = 0, rlog_chunk_log2 = 0, range_shift = 0, nranges = 0;
+  // Eq. 2 dedupe bit vectors (one per scan CTA) for passes with at most bitmap_bits slots
+  uint32_t* bitmap = nullptr;
+  uint64_t bitmap_bits = 0;
 };
 
 namespace {
@@ -164,7 +167,7 @@ void release(ig_plan* pl) {
                   pl->list_off[1], pl->list_cnt[0], pl->list_cnt[1], pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
                   pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank,
-                  pl->rlog, pl->rlog_range, pl->rlog_fill};
+                  pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap};
   for (void* q : ptrs)
     if (q) {
       if (pl->async_alloc) cudaFreeAsync(q, pl->stream);
@@ -260,6 +263,10 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
     a.rlog_chunk_log2 = pl->rlog_chunk_log2;
     a.range_shift = pl->range_shift;
     a.nranges = pl->nranges;
+  }
+  if (seq_mode && pl->bitmap && ns <= pl->bitmap_bits) {
+    a.bitmap = pl->bitmap;
+    a.bitmap_words = (uint32_t)((ns + 31) / 32);
   }
   a.ctl = pl->ctl;
   if (timing) cudaEventRecordWithFlags(pl->ev_scan0[ti], s, evf);
@@ -494,7 +501,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
       t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13 || t.list_pct > 200 ||
-      t.log_mode > 1 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
+      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
       (t.log_range_log2 && (t.log_range_log2 < 10 || t.log_range_log2 > 30)))
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;
@@ -646,6 +653,22 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
       PLAN_CUDA(dev_alloc(pl, &pl->rlog, chunks << cl));
       PLAN_CUDA(dev_alloc(pl, &pl->rlog_range, chunks));
       PLAN_CUDA(dev_alloc(pl, &pl->rlog_fill, chunks));
+    }
+  }
+  // Eq. 2 bit vectors: a pass whose slot space is small dedupes each sequence
+  // with one bit per slot (atomicOr; the bit vectors of all scan CTAs stay
+  // in L2) instead of the shared-memory set and its spill lists
+  if (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE && t.dedupe_bitmap != 1) {
+    size_t free_b = 0, total_b = 0;
+    PLAN_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const uint64_t budget_bits = t.dedupe_bitmap == 2 ? (uint64_t)total_b / 4 * 8 : (48ull << 20) * 8;
+    const uint64_t limit = std::min<uint64_t>(budget_bits / (uint64_t)pl->scan_grid, 0xFFFFFFFFull * 32);
+    uint64_t bits = 0;
+    for (uint64_t ns : {pl->nslots_base, pl->nslots_cand})
+      if (ns && ns <= limit) bits = std::max(bits, ns);
+    if (bits) {
+      pl->bitmap_bits = bits;
+      PLAN_CUDA(dev_alloc(pl, &pl->bitmap, (size_t)pl->scan_grid * ((bits + 31) / 32)));
     }
   }
   PLAN_CUDA(dev_alloc(pl, &pl->ctl, 1));

@@ -113,6 +113,11 @@ struct ScanArgs {
   uint32_t rlog_chunk_log2;
   uint32_t range_shift;
   uint32_t nranges;            // <= kLogMaxRanges
+  // Eq. 2 dedupe by bit vector (small slot spaces): CTA b owns bits
+  // [b * bitmap_words * 32, ...) of `bitmap`, one bit per slot, cleared at
+  // the start of each of its sequences; null = shared-memory set + spills
+  uint32_t* bitmap;
+  uint32_t bitmap_words;
   PassCtl* ctl;
 };
 

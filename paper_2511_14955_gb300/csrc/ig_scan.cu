@@ -47,6 +47,13 @@ __device__ __forceinline__ uint32_t probe_table(const uint4* __restrict__ table,
   return kEmpty32;
 }
 
+// The paper's per-sequence bit vector C_i: set bit `slot`; true if it was
+// clear (first occurrence of the slot in the sequence).
+__device__ __forceinline__ bool bitmap_first(uint32_t* bm, uint32_t slot) {
+  const uint32_t bit = 1u << (slot & 31u);
+  return (atomicOr(bm + (slot >> 5), bit) & bit) == 0u;
+}
+
 // Insert into the CTA-private global set; true if `slot` is new for this
 // (pass, sequence) epoch.
 __device__ __forceinline__ bool gset_insert(unsigned long long* set, uint32_t log2, uint32_t epoch,
@@ -244,17 +251,23 @@ __device__ __forceinline__ void log_close(const ScanArgs& a, const LogState& lg)
   if (c < kNoChunk) a.rlog_fill[c] = lg.fill[r] < size ? lg.fill[r] : size;
 }
 
-// Exact dedupe of src[lo, hi) in the (cleared) shared-memory set; each
-// distinct slot is registered once. Fits whenever hi - lo <= capacity / 2.
+// Exact dedupe of src[lo, hi) in a cleared table at the front of the
+// shared-memory set, sized to at least twice the entries (at most the whole
+// set); each distinct slot is registered once. Fits whenever hi - lo <=
+// capacity / 2.
 __device__ void insert_range(const ScanArgs& a, const LogState& lg, const uint32_t* src, uint32_t lo, uint32_t hi,
                              uint32_t* sset, unsigned long long& my_regs) {
-  const uint32_t tid = threadIdx.x, nthr = blockDim.x, cap = 1u << a.sset_log2;
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+  uint32_t slog = ceil_log2_u64(2ull * (hi - lo));
+  slog = slog < 8u ? 8u : slog;
+  slog = slog > a.sset_log2 ? a.sset_log2 : slog;
+  const uint32_t cap = 1u << slog;
   for (uint32_t i = tid; i < cap; i += nthr) sset[i] = kEmpty32;
   log_room(a, lg, hi - lo);
   __syncthreads();
   for (uint32_t i = lo + tid; i < hi; i += nthr) {
     const uint32_t v = src[i];
-    if (sset_insert_full(sset, a.sset_log2, v, a.ctl)) {
+    if (sset_insert_full(sset, slog, v, a.ctl)) {
       ++my_regs;
       register_slot(a, lg, v);
     }
@@ -357,6 +370,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   uint32_t* tile_alive = tile + a.tile_words + a.queue_words;
   const uint32_t alive_tile_words = (tile_windows + 31) / 32;
   unsigned long long* gset = a.gset ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
+  uint32_t* bm = a.bitmap ? a.bitmap + (uint64_t)blockIdx.x * a.bitmap_words : nullptr;
   // CTA-private spill list and partition buffer (Eq. 2 without a global set)
   uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
   uint32_t* spill_part = spill_list ? spill_list + a.spill_cap : nullptr;
@@ -392,7 +406,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
       if (slog < 1) slog = 1;
       glog = need < a.gset_log2 ? need : a.gset_log2;
       if (glog < 1) glog = 1;
-      for (uint32_t i = tid; i < (1u << slog); i += nthr) sset[i] = kEmpty32;
+      if (bm) {
+        for (uint32_t i = tid; i < a.bitmap_words; i += nthr) bm[i] = 0u;
+      } else {
+        for (uint32_t i = tid; i < (1u << slog); i += nthr) sset[i] = kEmpty32;
+      }
     }
     if (tid == 0) s_nspill = 0;
 
@@ -451,7 +469,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             ++my_surv;
             bool count_it = true;
             if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-              if (spill_list) {
+              if (bm) {
+                count_it = bitmap_first(bm, slot);
+              } else if (spill_list) {
                 const int r = sset_try_insert(sset, slog, slot);
                 count_it = (r == 1);
                 if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
@@ -473,27 +493,38 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           for (uint32_t i = tid; i < alive_tile_words; i += nthr) tile_alive[i] = 0;
         __syncthreads();
         const uint32_t lane = tid & 31;
-        const uint32_t total = wb < nwin ? ((wb + R < nwin ? R : nwin - wb) + j - 1) : 0u;
         if (a.alive_in) {
-          uint32_t in_idx = 0xFFFFFFFFu, in_word = 0;
-          for (uint32_t i = j - 1; i < R + j - 1; ++i) {
-            bool cand = false;
-            uint32_t w = 0;
-            if (i < total) {
-              w = wb + i + 1 - j;
-              const uint64_t gp = gsym + w;
-              if ((uint32_t)(gp >> 5) != in_idx) {
-                in_idx = (uint32_t)(gp >> 5);
-                in_word = __ldg(a.alive_in + (gp >> 5));
-              }
-              cand = (in_word >> (gp & 31)) & 1u;
+          // word-parallel: each thread takes whole 32-bit words of the
+          // survivor mask (corpus bits gsym .. gsym + nwin - 1), a warp scan
+          // places their set bits in the queue
+          const uint64_t k0 = gsym >> 5;
+          const uint32_t nwords = (uint32_t)(((gsym + nwin - 1) >> 5) - k0 + 1);
+          for (uint32_t kb = 0; kb < nwords; kb += nthr) {
+            const uint32_t k = kb + tid;
+            uint32_t bits = 0;
+            if (k < nwords) {
+              bits = __ldg(a.alive_in + k0 + k);
+              const uint64_t p0 = (k0 + k) << 5;  // corpus bit of bit 0
+              if (p0 < gsym) bits &= ~0u << (uint32_t)(gsym - p0);
+              const uint64_t end = gsym + nwin;  // first bit past the tile
+              if (p0 + 32 > end) bits &= (end - p0 >= 32) ? ~0u : ((1u << (uint32_t)(end - p0)) - 1u);
             }
-            const uint32_t m = __ballot_sync(0xffffffffu, cand);
-            if (m) {
-              uint32_t base = 0;
-              if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(&s_qn, (uint32_t)__popc(m));
-              base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-              if (cand) queue[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
+            const uint32_t c = __popc(bits);
+            uint32_t incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= (uint32_t)o) incl += v;
+            }
+            uint32_t base = 0;
+            const uint32_t wsum = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane == 31 && wsum) base = atomicAdd(&s_qn, wsum);
+            base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+            // tile window of bit b of word k: (k0 + k) * 32 + b - gsym
+            const uint32_t wbase = (uint32_t)(((k0 + k) << 5) - gsym);
+            while (bits) {
+              const uint32_t b = __ffs(bits) - 1;
+              bits &= bits - 1;
+              queue[base++] = (uint16_t)(wbase + b);
             }
           }
         } else {
@@ -552,7 +583,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           ++my_surv;
           bool count_it = true;
           if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-            if (spill_list) {
+            if (bm) {
+              count_it = bitmap_first(bm, slot);
+            } else if (spill_list) {
               const int r = sset_try_insert(sset, slog, slot);
               count_it = (r == 1);
               if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
@@ -621,22 +654,58 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
 // (keyed by slot) answers with the counter row of pass j. The last symbol is
 // read from the corpus. No tile is staged: work is proportional to the
 // survivors of pass j-1, and keys of any length stay exact.
+//
+// A CTA owns a sequence. Its runs (the run-table entries of all its tiles)
+// are taken in chunks: a block scan of the chunk's run sizes turns the runs
+// into one index space, each thread takes entries of that space (a binary
+// search finds an entry's run), and the chunk's survivors are written as one
+// run at the chunk's first index (the others stay empty). Only a few
+// barriers per chunk, however few survivors a tile has.
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < nw ? warp_tot[lane] : 0u, ti = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= (uint32_t)o) ti += u;
+    }
+    if (lane < nw) warp_tot[lane] = ti - t;   // exclusive warp offsets
+    if (lane == 31) warp_tot[32] = ti;        // block total
+  }
+  __syncthreads();
+  total = warp_tot[32];
+  return warp_tot[warp] + incl - v;
+}
+
 template <int SB>
 __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_item, s_nspill;
-  __shared__ unsigned long long s_surv, s_regs;
-  __shared__ unsigned long long s_run_off[kMaxRuns], s_run_base[kMaxRuns];
-  __shared__ uint32_t s_run_in[kMaxRuns], s_run_cnt[kMaxRuns];
+  __shared__ uint32_t s_item, s_nspill, s_out_cnt;
+  __shared__ unsigned long long s_surv, s_regs, s_out_base;
+  __shared__ uint32_t s_warp[33];
   __shared__ uint32_t s_log_chunk[kLogMaxRanges], s_log_fill[kLogMaxRanges];
   const LogState lg{s_log_chunk, s_log_fill};
   log_init(lg);
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
   uint32_t* sset = smem;
   uint32_t* scratch = smem + (1u << a.sset_log2);
+  const uint32_t scratch_words = a.tile_words + a.queue_words;
+  // run chunk in the scratch area: offsets (u64) then exclusive prefix sums
+  const uint32_t chunk_runs = (scratch_words - 2) / 3 < nthr ? (scratch_words - 2) / 3 : nthr;
+  unsigned long long* c_off = reinterpret_cast<unsigned long long*>(scratch);
+  uint32_t* c_pre = scratch + 2 * chunk_runs;
   uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
   uint32_t* spill_part = spill_list ? spill_list + a.spill_cap : nullptr;
-  const uint32_t j = a.j, T = a.tile_windows;
+  uint32_t* bm = a.bitmap ? a.bitmap + (uint64_t)blockIdx.x * a.bitmap_words : nullptr;
+  const uint32_t j = a.j;
+  const uint32_t step = a.rlog ? (1u << a.rlog_chunk_log2) >> 3 : 0xFFFFFFFFu;
   unsigned long long my_surv = 0, my_regs = 0;
   if (tid == 0) { s_surv = 0; s_regs = 0; }
 
@@ -656,47 +725,54 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
       const uint32_t need = ceil_log2_u64(2 * W);
       slog = need < a.sset_log2 ? need : a.sset_log2;
       if (slog < 1) slog = 1;
-      for (uint32_t i = tid; i < (1u << slog); i += nthr) sset[i] = kEmpty32;
+      if (bm) {
+        for (uint32_t i = tid; i < a.bitmap_words; i += nthr) bm[i] = 0u;
+      } else {
+        for (uint32_t i = tid; i < (1u << slog); i += nthr) sset[i] = kEmpty32;
+      }
     }
     if (tid == 0) s_nspill = 0;
-    const uint32_t g0 = a.tile_base[seq];
-    const uint32_t ntiles = (uint32_t)((W + 1 + T - 1) / T);   // tiles of pass j-1 (W + 1 windows)
+    // every run-table entry of the sequence's tiles (a fixed range for all passes)
+    const uint32_t x0 = a.tile_base[seq] * a.runs_per_tile, x1 = a.tile_base[seq + 1] * a.runs_per_tile;
     __syncthreads();
-    for (uint32_t t = 0; t < ntiles; ++t) {
-      // the tile's input runs, and (if a list is written) output run r
-      // reserved with room for every entry of input run r
-      const uint32_t run0 = (g0 + t) * a.runs_per_tile;
-      if (tid < a.runs_per_tile) {
-        const uint32_t c = a.list_in_cnt[run0 + tid];
-        s_run_in[tid] = c;
-        s_run_off[tid] = a.list_in_off[run0 + tid];
-        if (a.list_out) {
-          unsigned long long base = ~0ull;
-          if (c) {
-            base = atomicAdd(&a.ctl->list_used, (unsigned long long)c);
-            if (base + c > a.list_cap) {
-              atomicOr(&a.ctl->status, kStListFull);
-              base = ~0ull;
-            }
+    for (uint32_t c0 = x0; c0 < x1; c0 += chunk_runs) {
+      const uint32_t nr = (x1 - c0) < chunk_runs ? (x1 - c0) : chunk_runs;
+      uint32_t cnt = 0;
+      if (tid < nr) {
+        cnt = a.list_in_cnt[c0 + tid];
+        c_off[tid] = a.list_in_off[c0 + tid];
+      }
+      uint32_t total = 0;
+      const uint32_t pre = block_excl_sum(cnt, s_warp, total);
+      if (tid < nr) c_pre[tid] = pre;
+      if (tid == 0 && a.list_out) {
+        unsigned long long base = ~0ull;
+        if (total) {
+          base = atomicAdd(&a.ctl->list_used, (unsigned long long)total);
+          if (base + total > a.list_cap) {
+            atomicOr(&a.ctl->status, kStListFull);
+            base = ~0ull;
           }
-          s_run_base[tid] = base;
-          s_run_cnt[tid] = 0;
         }
+        s_out_base = base;
+        s_out_cnt = 0;
       }
       __syncthreads();
-      // runs in groups of at most chunk / 8 entries when registrations go to the log
-      const uint32_t group = a.rlog ? ((1u << a.rlog_chunk_log2) >> 3) / kRunChunk : a.runs_per_tile;
-      for (uint32_t r0 = 0; r0 < a.runs_per_tile; r0 += group) {
-      const uint32_t r1 = a.runs_per_tile - r0 < group ? a.runs_per_tile : r0 + group;
-      if (a.rlog) {
-        log_room(a, lg, (r1 - r0) * kRunChunk);
-        __syncthreads();
-      }
-      for (uint32_t r = r0; r < r1; ++r) {
-        const uint32_t n_in = s_run_in[r];
-        const unsigned long long off_in = s_run_off[r];
-        for (uint32_t e = tid; e < n_in; e += nthr) {
-          const unsigned long long ent = a.list_in[off_in + e];
+      for (uint32_t e0 = 0; e0 < total; e0 += step) {
+        const uint32_t e1 = total - e0 < step ? total : e0 + step;
+        if (a.rlog) {
+          log_room(a, lg, e1 - e0);
+          __syncthreads();
+        }
+        for (uint32_t e = e0 + tid; e < e1; e += nthr) {
+          // run of entry e: the last run whose prefix is <= e (it is not empty)
+          uint32_t lo = 0, hi = nr;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (c_pre[mid] <= e) lo = mid;
+            else hi = mid;
+          }
+          const unsigned long long ent = a.list_in[c_off[lo] + (e - c_pre[lo])];
           const uint32_t w = (uint32_t)ent;
           if (w >= W) continue;  // the last window of pass j-1 has no j-gram
           const uint64_t pos = s0 + w + j - 1;
@@ -710,32 +786,35 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
           if (id == kEmpty32) continue;
           const uint32_t slot = (id << SB) | sym;
           ++my_surv;
-          if (a.list_out && s_run_base[r] != ~0ull)
-            a.list_out[s_run_base[r] + atomicAdd(s_run_cnt + r, 1u)] = ((unsigned long long)slot << 32) | w;
+          if (a.list_out && s_out_base != ~0ull)
+            a.list_out[s_out_base + atomicAdd(&s_out_cnt, 1u)] = ((unsigned long long)slot << 32) | w;
           bool count_it = true;
           if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-            const int rr = sset_try_insert(sset, slog, slot);
-            count_it = (rr == 1);
-            if (rr == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+            if (bm) {
+              count_it = bitmap_first(bm, slot);
+            } else {
+              const int rr = sset_try_insert(sset, slog, slot);
+              count_it = (rr == 1);
+              if (rr == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+            }
           }
           if (count_it) {
             ++my_regs;
             register_slot(a, lg, slot);
           }
         }
-      }
-      if (a.rlog) __syncthreads();
+        if (a.rlog) __syncthreads();
       }
       __syncthreads();
-      if (a.list_out && tid < a.runs_per_tile) {
-        a.list_out_off[run0 + tid] = s_run_base[tid];
-        a.list_out_cnt[run0 + tid] = s_run_base[tid] == ~0ull ? 0u : s_run_cnt[tid];
+      if (tid == 0 && a.list_out && total) {
+        a.list_out_off[c0] = s_out_base;
+        a.list_out_cnt[c0] = s_out_base == ~0ull ? 0u : s_out_cnt;
       }
     }
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       __syncthreads();
       const uint32_t nsp = s_nspill;
-      if (nsp) dedupe_spills(a, lg, nsp, sset, scratch, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
+      if (nsp) dedupe_spills(a, lg, nsp, sset, scratch, scratch_words, spill_list, spill_part, my_regs);
     }
     __syncthreads();
   }

@@ -28,31 +28,47 @@ def oracle_rows(keys, symbol_bits):
     return np.stack([synth.pack_2bit(r) for r in keys]) if len(keys) else keys[:, : (keys.shape[1] + 3) // 4]
 
 
+def dedupe_variants(mode, tuning):
+    """Under Eq. 2 a pass dedupes by bit vector when its slot space is small,
+    else by the shared-memory set with spill lists: run both unless the
+    tuning picks one."""
+    tuning = dict(tuning or {})
+    if mode != O.EQ2_ONCE_PER_SEQUENCE or "dedupe_bitmap" in tuning:
+        return [tuning]
+    return [tuning, dict(tuning, dedupe_bitmap=1)]
+
+
 def check_all_passes(data, off, *, n, k, Z, base_n, mode=0, symbol_bits=8, tuning=None, graph=False):
-    d, o = dev(data, off)
-    pl = B.Plan(d, o, n=n, k=k, candidates=Z, base_n=base_n, symbol_bits=symbol_bits, count_mode=mode,
-                tuning=tuning, graph=graph)
     b = min(base_n, n)
-    seen = []
-    while True:
-        j = pl.step()
-        if j is None:
-            break
-        seen.append(j)
-        gk, gc, gj = pl.topk()
-        ek, ec = O.intergrams(data, off, n, k, Z, base_n=base_n, count_mode=mode, symbol_bits=symbol_bits,
-                              stop_j=j)
-        ek = oracle_rows(ek, symbol_bits)
-        assert gj == j
-        assert gk.shape == ek.shape, (j, gk.shape, ek.shape)
-        assert np.array_equal(gc, ec), f"counts differ at pass {j}"
-        assert np.array_equal(gk, ek), f"keys differ at pass {j}"
-        if mode == O.EQ1_EVERY_OCCURRENCE:
-            _, _, surv = O.intergrams(data, off, n, 1, Z, base_n=base_n, count_mode=mode,
-                                      symbol_bits=symbol_bits, stop_j=j, want_survivors=True)
-            assert pl.stats()["survivors"] == surv
-    assert seen == list(range(b, n + 1))
-    pl.close()
+    expect = {}
+    for tun in dedupe_variants(mode, tuning):
+        d, o = dev(data, off)
+        pl = B.Plan(d, o, n=n, k=k, candidates=Z, base_n=base_n, symbol_bits=symbol_bits, count_mode=mode,
+                    tuning=tun, graph=graph)
+        seen = []
+        while True:
+            j = pl.step()
+            if j is None:
+                break
+            seen.append(j)
+            gk, gc, gj = pl.topk()
+            if j not in expect:
+                ek, ec = O.intergrams(data, off, n, k, Z, base_n=base_n, count_mode=mode,
+                                      symbol_bits=symbol_bits, stop_j=j)
+                surv = None
+                if mode == O.EQ1_EVERY_OCCURRENCE:
+                    _, _, surv = O.intergrams(data, off, n, 1, Z, base_n=base_n, count_mode=mode,
+                                              symbol_bits=symbol_bits, stop_j=j, want_survivors=True)
+                expect[j] = (oracle_rows(ek, symbol_bits), ec, surv)
+            ek, ec, surv = expect[j]
+            assert gj == j
+            assert gk.shape == ek.shape, (tun, j, gk.shape, ek.shape)
+            assert np.array_equal(gc, ec), f"counts differ at pass {j} ({tun})"
+            assert np.array_equal(gk, ek), f"keys differ at pass {j} ({tun})"
+            if surv is not None:
+                assert pl.stats()["survivors"] == surv
+        assert seen == list(range(b, n + 1))
+        pl.close()
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -95,22 +111,26 @@ def test_results_do_not_depend_on_tuning(tuning):
 
 def check_passes(data, off, *, n, k, Z, base_n, js, mode=0, symbol_bits=8, tuning=None):
     """Run every pass; compare with the oracle after the passes in `js`."""
-    d, o = dev(data, off)
-    pl = B.Plan(d, o, n=n, k=k, candidates=Z, base_n=base_n, symbol_bits=symbol_bits, count_mode=mode,
-                tuning=tuning)
-    while True:
-        j = pl.step()
-        if j is None:
-            break
-        if j in js:
-            gk, gc, gj = pl.topk()
-            ek, ec = O.intergrams(data, off, n, k, Z, base_n=base_n, count_mode=mode, symbol_bits=symbol_bits,
-                                  stop_j=j)
-            ek = oracle_rows(ek, symbol_bits)
-            assert gk.shape == ek.shape, (j, gk.shape, ek.shape)
-            assert np.array_equal(gc, ec), f"counts differ at pass {j}"
-            assert np.array_equal(gk, ek), f"keys differ at pass {j}"
-    pl.close()
+    expect = {}
+    for tun in dedupe_variants(mode, tuning):
+        d, o = dev(data, off)
+        pl = B.Plan(d, o, n=n, k=k, candidates=Z, base_n=base_n, symbol_bits=symbol_bits, count_mode=mode,
+                    tuning=tun)
+        while True:
+            j = pl.step()
+            if j is None:
+                break
+            if j in js:
+                gk, gc, gj = pl.topk()
+                if j not in expect:
+                    ek, ec = O.intergrams(data, off, n, k, Z, base_n=base_n, count_mode=mode,
+                                          symbol_bits=symbol_bits, stop_j=j)
+                    expect[j] = (oracle_rows(ek, symbol_bits), ec)
+                ek, ec = expect[j]
+                assert gk.shape == ek.shape, (tun, j, gk.shape, ek.shape)
+                assert np.array_equal(gc, ec), f"counts differ at pass {j} ({tun})"
+                assert np.array_equal(gk, ek), f"keys differ at pass {j} ({tun})"
+        pl.close()
 
 
 @pytest.mark.parametrize("mode", [0, 1])
