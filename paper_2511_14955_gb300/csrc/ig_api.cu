@@ -192,6 +192,9 @@ uint32_t mode_of(const ig_plan* pl, uint32_t j) {
   return kModeShort;
 }
 
+// Kernels of one sort by count: init + (histogram, two scans, scatter) per 8-bit digit.
+uint32_t sort_kernels(const ig_plan* pl) { return 1 + 4 * (pl->narrow ? 2u : 4u); }
+
 // Enqueue pass j (no host synchronisation); returns the kernels launched.
 uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   const uint32_t md = mode_of(pl, j), md_next = mode_of(pl, j + 1);
@@ -295,11 +298,11 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
       launch_build_keys(sel, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], s);
     else
       launch_chain_keys(sel, pl->ctl, pl->rank, base, pl->sb, pl->keys[nxt], s);
-    launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
+    launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->narrow ? 16u : 32u, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
                          pl->shist, s);
     launch_rank(pl->sidx[0], pl->ctl, pl->rank, pl->p.candidates, s);
     launch_build_table(pl->keys[nxt], pl->rank, pl->ctl, pl->table, pl->table_log2, s);
-    kernels += 1 + 13 + 2 + 2;
+    kernels += 1 + sort_kernels(pl) + 2 + 2;
     if (pl->hot_log2 && md_next == kModeShort) {
       launch_build_hot(pl->keys[nxt], pl->sel_count, pl->rank, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
       kernels += 3;
@@ -371,12 +374,12 @@ ig_status plan_enqueue_topk(ig_plan* pl, uint8_t* keys_host, uint64_t* counts_ho
   *rows = r;
   cudaStream_t s = pl->stream;
   if (r) {
-    launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
+    launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->narrow ? 16u : 32u, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
                          pl->shist, s);
     const uint32_t rb = row_bytes_for(pl, j);
     launch_write_topk(pl->sel_hist, pl->p.candidates, pl->b, pl->sel_count, pl->sidx[0], pl->ctl, pl->sb, j, rb, r,
                       pl->out_keys, pl->out_counts, s);
-    pl->kernels += 14;
+    pl->kernels += sort_kernels(pl) + 1;
     IG_CUDA(cudaMemcpyAsync(keys_host, pl->out_keys, (size_t)r * rb, cudaMemcpyDeviceToHost, s));
     IG_CUDA(cudaMemcpyAsync(counts_host, pl->out_counts, (size_t)r * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   }
@@ -599,7 +602,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   PLAN_CUDA(dev_alloc(pl, &pl->sidx[1], pl->sort_cap));
   PLAN_CUDA(dev_alloc(pl, &pl->skey[0], pl->sort_cap));
   PLAN_CUDA(dev_alloc(pl, &pl->skey[1], pl->sort_cap));
-  PLAN_CUDA(dev_alloc(pl, &pl->shist, (size_t)kSortDigits * sortG));
+  PLAN_CUDA(dev_alloc(pl, &pl->shist, (size_t)kSortDigits * (sortG + 1)));
   if (pl->spill_cap) PLAN_CUDA(dev_alloc(pl, &pl->spill, (size_t)pl->scan_grid * 2 * pl->spill_cap));
   PLAN_CUDA(dev_alloc(pl, &pl->d_tile_base, (size_t)m + 1));
   if (!pl->dry_run)
@@ -781,13 +784,13 @@ ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out, 
   const uint32_t rows = std::min(std::min(pl->p.k, capacity), pl->nsel_last);
   if (rows == 0) return IG_OK;
   cudaStream_t s = pl->stream;
-  launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
+  launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->narrow ? 16u : 32u, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
                        pl->shist, s);
   // symbols of each selected j-gram: walk back through every pass's selection
   const uint32_t rb = row_bytes_for(pl, j);
   launch_write_topk(pl->sel_hist, pl->p.candidates, pl->b, pl->sel_count, pl->sidx[0], pl->ctl, pl->sb, j, rb, rows,
                     pl->out_keys, pl->out_counts, s);
-  pl->kernels += 14;  // sort: init + 4 x (histogram, scan, scatter); write
+  pl->kernels += sort_kernels(pl) + 1;  // sort, then the row writer
   IG_CUDA(cudaGetLastError());
   if (keys_out) IG_CUDA(cudaMemcpyAsync(keys_out, pl->out_keys, (size_t)rows * rb, cudaMemcpyDeviceToHost, s));
   if (counts_out)

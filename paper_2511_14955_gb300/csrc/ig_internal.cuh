@@ -145,9 +145,11 @@ void launch_select(const uint32_t* counts, bool narrow, const uint32_t* rank, ui
                    uint32_t* blk /* 2*G */, int G, uint32_t* sel_slot, uint32_t* sel_count, cudaStream_t s);
 // rank[order[x]] = x for the nsel selected candidates, rank[i] = i beyond
 void launch_rank(const uint32_t* order, const PassCtl* ctl, uint32_t* rank, uint32_t n, cudaStream_t s);
-void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap,
+// stable LSD radix sort of the selected entries by count, descending; key_bits
+// 16 when every count is < 65536 (two digit passes), else 32 (four)
+void launch_sort_by_count(const uint32_t* sel_count, PassCtl* ctl, uint32_t cap, uint32_t key_bits,
                           uint32_t* idx_a, uint32_t* idx_b, uint32_t* key_a, uint32_t* key_b,
-                          uint32_t* hist /* kSortDigits * ceil(cap/kSortChunk) */, cudaStream_t s);
+                          uint32_t* hist /* kSortDigits * (ceil(cap/kSortChunk) + 1) */, cudaStream_t s);
 
 // Launchers (ig_table.cu)
 // keys_next[r] = key of selected slot r; ids are in byte order

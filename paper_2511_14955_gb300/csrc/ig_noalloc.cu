@@ -53,7 +53,7 @@ Layout layout() {
   L.idx1 = take(sizeof(uint32_t) * kMaxSlots);
   L.key0 = take(sizeof(uint32_t) * kMaxSlots);
   L.key1 = take(sizeof(uint32_t) * kMaxSlots);
-  L.shist = take(sizeof(uint32_t) * kSortDigits * (kMaxSlots / kSortChunk));
+  L.shist = take(sizeof(uint32_t) * kSortDigits * (kMaxSlots / kSortChunk + 1));
   L.order = take(sizeof(uint32_t) * kMaxSeqs);
   L.gset = take(sizeof(unsigned long long) * ((size_t)kGrid << kGsetLog2));
   L.end = o;
@@ -161,7 +161,7 @@ extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void
   launch_select(counts, false, nullptr, sb, nslots, p->k, ctl, reinterpret_cast<uint32_t*>(S + L.hist),
                 reinterpret_cast<uint32_t*>(S + L.blk), 1024, reinterpret_cast<uint32_t*>(S + L.sel_slot),
                 reinterpret_cast<uint32_t*>(S + L.sel_count), s);
-  launch_sort_by_count(reinterpret_cast<uint32_t*>(S + L.sel_count), ctl, kMaxSlots,
+  launch_sort_by_count(reinterpret_cast<uint32_t*>(S + L.sel_count), ctl, kMaxSlots, 32u,
                        reinterpret_cast<uint32_t*>(S + L.idx0), reinterpret_cast<uint32_t*>(S + L.idx1),
                        reinterpret_cast<uint32_t*>(S + L.key0), reinterpret_cast<uint32_t*>(S + L.key1),
                        reinterpret_cast<uint32_t*>(S + L.shist), s);
