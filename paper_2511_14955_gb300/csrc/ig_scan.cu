@@ -162,6 +162,17 @@ __device__ __forceinline__ bool sset_insert_full(uint32_t* sset, uint32_t slog, 
   return false;
 }
 
+// Append `slot` to the spill list: one shared-memory atomic per warp among
+// the lanes spilling together.
+__device__ __forceinline__ void spill_push(uint32_t* list, uint32_t* n, uint32_t slot) {
+  const uint32_t peers = __activemask();
+  const uint32_t lane = threadIdx.x & 31u, leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(n, (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  list[base + __popc(peers & ((1u << lane) - 1u))] = slot;
+}
+
 // Bucket bits of a spilled slot: bits [shift, shift + kb) (from the top) of
 // the murmur3 32-bit finaliser (Appleby), unrelated to the multiply-shift
 // bits that index the shared-memory set.
@@ -251,6 +262,34 @@ __device__ __forceinline__ void log_close(const ScanArgs& a, const LogState& lg)
   if (c < kNoChunk) a.rlog_fill[c] = lg.fill[r] < size ? lg.fill[r] : size;
 }
 
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < nw ? warp_tot[lane] : 0u, ti = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= (uint32_t)o) ti += u;
+    }
+    if (lane < nw) warp_tot[lane] = ti - t;   // exclusive warp offsets
+    if (lane == 31) warp_tot[32] = ti;        // block total
+  }
+  __syncthreads();
+  total = warp_tot[32];
+  return warp_tot[warp] + incl - v;
+}
+
+// Global-memory loops below take kBatch entries per thread per round, all
+// loaded before any is used, so enough loads are in flight to cover memory
+// latency with one CTA per SM.
+constexpr uint32_t kBatch = 8;
+
 // Exact dedupe of src[lo, hi) in a cleared table at the front of the
 // shared-memory set, sized to at least twice the entries (at most the whole
 // set); each distinct slot is registered once. Fits whenever hi - lo <=
@@ -265,11 +304,16 @@ __device__ void insert_range(const ScanArgs& a, const LogState& lg, const uint32
   for (uint32_t i = tid; i < cap; i += nthr) sset[i] = kEmpty32;
   log_room(a, lg, hi - lo);
   __syncthreads();
-  for (uint32_t i = lo + tid; i < hi; i += nthr) {
-    const uint32_t v = src[i];
-    if (sset_insert_full(sset, slog, v, a.ctl)) {
-      ++my_regs;
-      register_slot(a, lg, v);
+  for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
+    uint32_t v[kBatch];
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) {
+      if (i0 + k * nthr < hi && sset_insert_full(sset, slog, v[k], a.ctl)) {
+        ++my_regs;
+        register_slot(a, lg, v[k]);
+      }
     }
   }
   __syncthreads();
@@ -279,20 +323,41 @@ __device__ void insert_range(const ScanArgs& a, const LogState& lg, const uint32
 // bucket b ends up in dst[bnd[b], bnd[b + 1]).
 __device__ void partition_range(const uint32_t* src, uint32_t* dst, uint32_t lo, uint32_t hi, uint32_t shift,
                                 uint32_t kb, uint32_t* bnd, uint32_t* cur) {
+  __shared__ uint32_t s_wt[33];
   const uint32_t tid = threadIdx.x, nthr = blockDim.x, K = 1u << kb;
   for (uint32_t b = tid; b < K; b += nthr) bnd[b] = 0;
   __syncthreads();
-  for (uint32_t i = lo + tid; i < hi; i += nthr) atomicAdd(bnd + spill_bucket(src[i], shift, kb), 1u);
-  __syncthreads();
-  if (tid == 0) {
-    uint32_t run = lo;
-    for (uint32_t b = 0; b < K; ++b) { const uint32_t c = bnd[b]; bnd[b] = run; cur[b] = run; run += c; }
-    bnd[K] = hi;
+  for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
+    uint32_t v[kBatch];
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k)
+      if (i0 + k * nthr < hi) atomicAdd(bnd + spill_bucket(v[k], shift, kb), 1u);
   }
   __syncthreads();
-  for (uint32_t i = lo + tid; i < hi; i += nthr) {
-    const uint32_t v = src[i];
-    dst[atomicAdd(cur + spill_bucket(v, shift, kb), 1u)] = v;
+  // bucket starts: each thread scans a run of consecutive buckets
+  const uint32_t per = (K + nthr - 1) / nthr, b0 = tid * per, b1 = b0 + per < K ? b0 + per : K;
+  uint32_t mine = 0;
+  for (uint32_t b = b0; b < b1; ++b) mine += bnd[b];
+  uint32_t total = 0;
+  uint32_t run = lo + block_excl_sum(mine, s_wt, total);
+  __syncthreads();
+  for (uint32_t b = b0; b < b1; ++b) {
+    const uint32_t c = bnd[b];
+    bnd[b] = run;
+    cur[b] = run;
+    run += c;
+  }
+  if (tid == 0) bnd[K] = hi;
+  __syncthreads();
+  for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
+    uint32_t v[kBatch];
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k)
+      if (i0 + k * nthr < hi) dst[atomicAdd(cur + spill_bucket(v[k], shift, kb), 1u)] = v[k];
   }
   __syncthreads();
 }
@@ -474,7 +539,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               } else if (spill_list) {
                 const int r = sset_try_insert(sset, slog, slot);
                 count_it = (r == 1);
-                if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+                if (r == 2) spill_push(spill_list, &s_nspill, slot);
               } else {
                 count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
               }
@@ -588,7 +653,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             } else if (spill_list) {
               const int r = sset_try_insert(sset, slog, slot);
               count_it = (r == 1);
-              if (r == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+              if (r == 2) spill_push(spill_list, &s_nspill, slot);
             } else {
               count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
             }
@@ -661,29 +726,6 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
 // search finds an entry's run), and the chunk's survivors are written as one
 // run at the chunk's first index (the others stay empty). Only a few
 // barriers per chunk, however few survivors a tile has.
-__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t incl = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= (uint32_t)o) incl += t;
-  }
-  if (lane == 31) warp_tot[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t t = lane < nw ? warp_tot[lane] : 0u, ti = t;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
-      if (lane >= (uint32_t)o) ti += u;
-    }
-    if (lane < nw) warp_tot[lane] = ti - t;   // exclusive warp offsets
-    if (lane == 31) warp_tot[32] = ti;        // block total
-  }
-  __syncthreads();
-  total = warp_tot[32];
-  return warp_tot[warp] + incl - v;
-}
-
 template <int SB>
 __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -795,7 +837,7 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
             } else {
               const int rr = sset_try_insert(sset, slog, slot);
               count_it = (rr == 1);
-              if (rr == 2) spill_list[atomicAdd(&s_nspill, 1u)] = slot;
+              if (rr == 2) spill_push(spill_list, &s_nspill, slot);
             }
           }
           if (count_it) {
