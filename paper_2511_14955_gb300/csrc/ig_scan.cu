@@ -54,6 +54,22 @@ __device__ __forceinline__ bool bitmap_first(uint32_t* bm, uint32_t slot) {
   return (atomicOr(bm + (slot >> 5), bit) & bit) == 0u;
 }
 
+// probe_table with the entry at the prefix's home position already loaded.
+__device__ __forceinline__ uint32_t probe_from(const uint4* __restrict__ table, uint32_t log2, uint64_t prefix,
+                                               uint4 e, PassCtl* ctl) {
+  const uint32_t mask = (1u << log2) - 1u;
+  uint32_t h = hash64_top(prefix, log2);
+  const uint32_t lo = (uint32_t)prefix, hi = (uint32_t)(prefix >> 32);
+  for (uint32_t it = 0; it <= mask; ++it) {
+    if (e.z == kEmpty32) return kEmpty32;
+    if (e.x == lo && e.y == hi) return e.z;
+    h = (h + 1) & mask;
+    e = __ldg(table + h);
+  }
+  atomicOr(&ctl->status, kStTableFull);
+  return kEmpty32;
+}
+
 // Insert into the CTA-private global set; true if `slot` is new for this
 // (pass, sequence) epoch.
 __device__ __forceinline__ bool gset_insert(unsigned long long* set, uint32_t log2, uint32_t epoch,
@@ -289,6 +305,7 @@ __device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* warp_to
 // loaded before any is used, so enough loads are in flight to cover memory
 // latency with one CTA per SM.
 constexpr uint32_t kBatch = 8;
+constexpr uint32_t kProbeBatch = 4;
 
 // Exact dedupe of src[lo, hi) in a cleared table at the front of the
 // shared-memory set, sized to at least twice the entries (at most the whole
@@ -626,41 +643,63 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           log_room(a, lg, q1 - q0);
           __syncthreads();
         }
-        for (uint32_t qi = q0 + tid; qi < q1; qi += nthr) {
-          const uint32_t w = queue[qi];
-          const uint64_t prefix = tile_key<SB>(tile, sym_off + w, j - 1);
-          const uint32_t last = tile_sym<SB>(tile, sym_off + w + j - 1);
-          uint32_t id = kEmpty32;
-          if (H) {
-            const uint32_t h = hash64_top(prefix, a.hot_log2);
-            if (hot_keys[h] == prefix) id = hot_ids[h];
-          }
-          if (id == kEmpty32) id = probe_table(a.table, a.table_log2, prefix, a.ctl);
-          if (id == kEmpty32) continue;
-          const uint32_t slot = (id << SB) | last;
-          if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
-          if (a.list_out) {
-            const uint32_t r = qi / kRunChunk;
-            if (s_run_base[r] != ~0ull)
-              a.list_out[s_run_base[r] + atomicAdd(s_run_cnt + r, 1u)] =
-                  ((unsigned long long)slot << 32) | (uint32_t)(w0 + w);
-          }
-          ++my_surv;
-          bool count_it = true;
-          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-            if (bm) {
-              count_it = bitmap_first(bm, slot);
-            } else if (spill_list) {
-              const int r = sset_try_insert(sset, slog, slot);
-              count_it = (r == 1);
-              if (r == 2) spill_push(spill_list, &s_nspill, slot);
-            } else {
-              count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
+        // kProbeBatch queued windows per thread per round: the probe-table
+        // loads of a round's hot-cache misses are all issued before any is used
+        for (uint32_t qb = q0 + tid; qb < q1; qb += kProbeBatch * nthr) {
+          uint64_t prefix[kProbeBatch];
+          uint32_t wl[kProbeBatch], id[kProbeBatch];
+          uint4 e[kProbeBatch];
+#pragma unroll
+          for (uint32_t k = 0; k < kProbeBatch; ++k) {
+            const uint32_t qi = qb + k * nthr;
+            id[k] = kEmpty32;
+            wl[k] = 0xFFFFFFFFu;  // not a window
+            prefix[k] = 0;
+            if (qi < q1) {
+              const uint32_t w = queue[qi];
+              prefix[k] = tile_key<SB>(tile, sym_off + w, j - 1);
+              wl[k] = (w << 8) | tile_sym<SB>(tile, sym_off + w + j - 1);
+              if (H) {
+                const uint32_t h = hash64_top(prefix[k], a.hot_log2);
+                if (hot_keys[h] == prefix[k]) id[k] = hot_ids[h];
+              }
             }
+            e[k] = make_uint4(0, 0, 0, 0);
+            if (wl[k] != 0xFFFFFFFFu && id[k] == kEmpty32)
+              e[k] = __ldg(a.table + hash64_top(prefix[k], a.table_log2));
           }
-          if (count_it) {
-            ++my_regs;
-            register_slot(a, lg, slot);
+#pragma unroll
+          for (uint32_t k = 0; k < kProbeBatch; ++k) {
+            if (wl[k] == 0xFFFFFFFFu) continue;
+            if (id[k] == kEmpty32) id[k] = probe_from(a.table, a.table_log2, prefix[k], e[k], a.ctl);
+            if (id[k] == kEmpty32) continue;
+            const uint32_t qi = qb + k * nthr;
+            const uint32_t w = wl[k] >> 8, last = wl[k] & 255u;
+            const uint32_t slot = (id[k] << SB) | last;
+            if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
+            if (a.list_out) {
+              const uint32_t r = qi / kRunChunk;
+              if (s_run_base[r] != ~0ull)
+                a.list_out[s_run_base[r] + atomicAdd(s_run_cnt + r, 1u)] =
+                    ((unsigned long long)slot << 32) | (uint32_t)(w0 + w);
+            }
+            ++my_surv;
+            bool count_it = true;
+            if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+              if (bm) {
+                count_it = bitmap_first(bm, slot);
+              } else if (spill_list) {
+                const int r = sset_try_insert(sset, slog, slot);
+                count_it = (r == 1);
+                if (r == 2) spill_push(spill_list, &s_nspill, slot);
+              } else {
+                count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
+              }
+            }
+            if (count_it) {
+              ++my_regs;
+              register_slot(a, lg, slot);
+            }
           }
         }
         if (a.rlog) __syncthreads();
