@@ -107,6 +107,10 @@ typedef struct {
                                 lists: 0 = auto (when the scan CTAs' bit vectors take at most
                                 48 MiB), 1 = never, 2 = whenever they fit in a quarter of the
                                 device memory */
+  uint32_t dense_prefix;     /* first candidate pass (j = base_n + 1): look the base-length prefix up
+                                in a dense map of sigma^base_n rows instead of the probe table:
+                                0 = auto (when the map and the counter array take at most
+                                112 MiB together, so both stay in L2), 1 = off, 2 = on */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -127,6 +127,8 @@ struct ig_plan {
   // Eq. 2 dedupe bit vectors (one per scan CTA) for passes with at most bitmap_bits slots
   uint32_t* bitmap = nullptr;
   uint64_t bitmap_bits = 0;
+  // dense prefix map of the first candidate pass (sigma^b rows)
+  uint32_t* dmap = nullptr;
 };
 
 namespace {
@@ -167,7 +169,7 @@ void release(ig_plan* pl) {
                   pl->list_off[1], pl->list_cnt[0], pl->list_cnt[1], pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
                   pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank,
-                  pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap};
+                  pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap, pl->dmap};
   for (void* q : ptrs)
     if (q) {
       if (pl->async_alloc) cudaFreeAsync(q, pl->stream);
@@ -190,6 +192,12 @@ uint32_t mode_of(const ig_plan* pl, uint32_t j) {
   if (j == pl->b + 1) return kModeShort;
   if ((j - 1) * pl->sb > 64 || j >= pl->chain_from) return kModeChain;
   return kModeShort;
+}
+
+// Pass j looks its prefixes up in the dense map (first candidate pass, not
+// followed by a chain pass, which needs survivor lists).
+bool dense_pass(const ig_plan* pl, uint32_t j) {
+  return pl->dmap && j == pl->b + 1 && mode_of(pl, j) == kModeShort && mode_of(pl, j + 1) != kModeChain;
 }
 
 // Kernels of one sort by count: init + (histogram, two scans, scatter) per 8-bit digit.
@@ -258,6 +266,10 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   }
   a.hot = pl->hot;
   a.hot_log2 = (md == kModeShort) ? pl->hot_log2 : 0u;
+  if (dense_pass(pl, j)) {
+    a.dmap = pl->dmap;
+    a.hot_log2 = 0;
+  }
   if (!base && pl->rlog) {
     a.rlog = pl->rlog;
     a.rlog_range = pl->rlog_range;
@@ -301,9 +313,15 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
     launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->narrow ? 16u : 32u, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
                          pl->shist, s);
     launch_rank(pl->sidx[0], pl->ctl, pl->rank, pl->p.candidates, s);
-    launch_build_table(pl->keys[nxt], pl->rank, pl->ctl, pl->table, pl->table_log2, s);
-    kernels += 1 + sort_kernels(pl) + 2 + 2;
-    if (pl->hot_log2 && md_next == kModeShort) {
+    kernels += 1 + sort_kernels(pl) + 2;
+    if (dense_pass(pl, j + 1)) {
+      launch_build_dmap(sel, pl->ctl, pl->rank, pl->dmap, pl->nslots_base, s);
+      kernels += 1;
+    } else {
+      launch_build_table(pl->keys[nxt], pl->rank, pl->ctl, pl->table, pl->table_log2, s);
+      kernels += 2;
+    }
+    if (pl->hot_log2 && md_next == kModeShort && !dense_pass(pl, j + 1)) {
       launch_build_hot(pl->keys[nxt], pl->sel_count, pl->rank, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
       kernels += 3;
     }
@@ -504,7 +522,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
       t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13 || t.list_pct > 200 ||
-      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
+      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.dense_prefix > 2 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
       (t.log_range_log2 && (t.log_range_log2 < 10 || t.log_range_log2 > 30)))
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;
@@ -657,6 +675,14 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
       PLAN_CUDA(dev_alloc(pl, &pl->rlog_range, chunks));
       PLAN_CUDA(dev_alloc(pl, &pl->rlog_fill, chunks));
     }
+  }
+  // dense prefix map for pass b + 1 when it and the counter array fit in L2
+  // together (else the probe table with its hot cache wins: measured)
+  {
+    const uint64_t cbytes = pl->nslots_cand * (pl->narrow ? 2u : 4u), mbytes = pl->nslots_base * 4u;
+    const bool want = t.dense_prefix == 2 || (t.dense_prefix == 0 && cbytes + mbytes <= (112ull << 20));
+    if (want && pl->b < p->n && mode_of(pl, pl->b + 1) == kModeShort && mode_of(pl, pl->b + 2) != kModeChain)
+      PLAN_CUDA(dev_alloc(pl, &pl->dmap, pl->nslots_base));
   }
   // Eq. 2 bit vectors: a pass whose slot space is small dedupes each sequence
   // with one bit per slot (atomicOr; the bit vectors of all scan CTAs stay

@@ -118,6 +118,9 @@ struct ScanArgs {
   // the start of each of its sequences; null = shared-memory set + spills
   uint32_t* bitmap;
   uint32_t bitmap_words;
+  // first candidate pass (j = base + 1, j * symbol_bits <= 32): counter row of
+  // every base-length prefix, kEmpty32 = not a candidate; null = probe table
+  const uint32_t* dmap;
   PassCtl* ctl;
 };
 
@@ -158,6 +161,9 @@ void launch_build_keys(const uint32_t* sel_slot, const PassCtl* ctl, const unsig
 // probe table: key -> rank[r] (the counter row the next scan uses)
 void launch_build_table(const unsigned long long* keys, const uint32_t* rank, const PassCtl* ctl, uint4* table,
                         uint32_t table_log2, cudaStream_t s);
+// dense prefix map after the base pass: dmap[sel_slot[i]] = rank[i], the rest kEmpty32
+void launch_build_dmap(const uint32_t* sel_slot, const PassCtl* ctl, const uint32_t* rank, uint32_t* dmap,
+                       uint64_t entries, cudaStream_t s);
 void launch_build_hot(const unsigned long long* keys, const uint32_t* sel_count, const uint32_t* rank,
                       const PassCtl* ctl, uint4* hot, unsigned long long* hot_pick, uint32_t hot_log2,
                       cudaStream_t s);

@@ -567,6 +567,89 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             }
           }
         }
+      } else if (a.dmap) {
+        // first candidate pass with a dense prefix map: every window is a
+        // candidate, so each thread rolls the key over its own run of
+        // windows as in the base pass; the (j-1)-gram prefix indexes the map
+        // directly (kProbeBatch map loads in flight per thread)
+        if (a.alive_out)
+          for (uint32_t i = tid; i < alive_tile_words; i += nthr) tile_alive[i] = 0;
+        __syncthreads();
+        if (wb < nwin) {
+          const uint32_t we = (wb + R) < nwin ? (wb + R) : nwin;
+          const uint32_t kmask = (uint32_t)a.key_mask;  // j * SB <= 32 here
+          uint32_t s = sym_off + wb;
+          uint32_t widx = s / S::kPerWord, q = s % S::kPerWord;
+          uint32_t word = bswap32(tile[widx]);
+          uint32_t key = 0;
+#define IG_NEXT_SYM(dst)                                                   \
+  do {                                                                     \
+    (dst) = (word >> (32 - SB * (q + 1))) & S::kMask;                      \
+    if (++q == S::kPerWord) {                                              \
+      q = 0;                                                               \
+      ++widx;                                                              \
+      word = (widx < a.tile_words) ? bswap32(tile[widx]) : 0u;             \
+    }                                                                      \
+  } while (0)
+          for (uint32_t i = 0; i + 1 < j; ++i) {
+            uint32_t sym;
+            IG_NEXT_SYM(sym);
+            key = ((key << SB) | sym) & kmask;
+          }
+          for (uint32_t w = wb; w < we; w += kProbeBatch) {
+            uint32_t kk[kProbeBatch], rk[kProbeBatch];
+#pragma unroll
+            for (uint32_t k = 0; k < kProbeBatch; ++k) {
+              rk[k] = kEmpty32;
+              kk[k] = 0;
+              if (w + k < we) {
+                uint32_t sym;
+                IG_NEXT_SYM(sym);
+                key = ((key << SB) | sym) & kmask;
+                kk[k] = key;
+                rk[k] = __ldg(a.dmap + (key >> SB));
+              }
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < kProbeBatch; ++k) {
+              if (rk[k] == kEmpty32) continue;
+              const uint32_t slot = (rk[k] << SB) | (kk[k] & S::kMask);
+              const uint32_t wt = w + k;
+              if (a.alive_out) atomicOr(tile_alive + (wt >> 5), 1u << (wt & 31));
+              ++my_surv;
+              bool count_it = true;
+              if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+                if (bm) {
+                  count_it = bitmap_first(bm, slot);
+                } else if (spill_list) {
+                  const int r = sset_try_insert(sset, slog, slot);
+                  count_it = (r == 1);
+                  if (r == 2) spill_push(spill_list, &s_nspill, slot);
+                } else {
+                  count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
+                }
+              }
+              if (count_it) {
+                ++my_regs;
+                register_slot(a, lg, slot);
+              }
+            }
+          }
+#undef IG_NEXT_SYM
+        }
+        if (a.alive_out) {
+          __syncthreads();
+          // tile bit w is corpus bit gsym + w
+          const uint32_t off = (uint32_t)(gsym & 31);
+          const uint64_t g0 = gsym >> 5;
+          const uint32_t nw = (nwin + off + 31) / 32;
+          for (uint32_t k = tid; k < nw; k += nthr) {
+            const uint32_t cur = k < alive_tile_words ? tile_alive[k] : 0u;
+            const uint32_t prev = (k > 0 && off) ? tile_alive[k - 1] : 0u;
+            const uint32_t v = off ? ((cur << off) | (prev >> (32 - off))) : cur;
+            if (v) atomicOr(a.alive_out + g0 + k, v);
+          }
+        }
       } else {
         // phase A: every thread walks its run of windows; alive ones are
         // queued (warp-aggregated), so phase B can process them densely
@@ -845,43 +928,65 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
           log_room(a, lg, e1 - e0);
           __syncthreads();
         }
-        for (uint32_t e = e0 + tid; e < e1; e += nthr) {
-          // run of entry e: the last run whose prefix is <= e (it is not empty)
-          uint32_t lo = 0, hi = nr;
-          while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (c_pre[mid] <= e) lo = mid;
-            else hi = mid;
-          }
-          const unsigned long long ent = a.list_in[c_off[lo] + (e - c_pre[lo])];
-          const uint32_t w = (uint32_t)ent;
-          if (w >= W) continue;  // the last window of pass j-1 has no j-gram
-          const uint64_t pos = s0 + w + j - 1;
-          uint32_t sym;
-          if (SB == 8) {
-            sym = __ldg(a.data + pos);
-          } else {
-            sym = (__ldg(a.data + (pos >> 2)) >> (6 - 2 * (pos & 3))) & 3u;
-          }
-          const uint32_t id = probe_table(a.table, a.table_log2, ent >> 32, a.ctl);
-          if (id == kEmpty32) continue;
-          const uint32_t slot = (id << SB) | sym;
-          ++my_surv;
-          if (a.list_out && s_out_base != ~0ull)
-            a.list_out[s_out_base + atomicAdd(&s_out_cnt, 1u)] = ((unsigned long long)slot << 32) | w;
-          bool count_it = true;
-          if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
-            if (bm) {
-              count_it = bitmap_first(bm, slot);
-            } else {
-              const int rr = sset_try_insert(sset, slog, slot);
-              count_it = (rr == 1);
-              if (rr == 2) spill_push(spill_list, &s_nspill, slot);
+        // kProbeBatch entries per thread per round: entry, corpus and
+        // probe-table loads of a round are issued before any result is used
+        for (uint32_t eb = e0 + tid; eb < e1; eb += kProbeBatch * nthr) {
+          unsigned long long ent[kProbeBatch];
+#pragma unroll
+          for (uint32_t k = 0; k < kProbeBatch; ++k) {
+            const uint32_t e = eb + k * nthr;
+            ent[k] = ~0ull;  // no entry
+            if (e < e1) {
+              // run of entry e: the last run whose prefix is <= e (it is not empty)
+              uint32_t lo = 0, hi = nr;
+              while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (c_pre[mid] <= e) lo = mid;
+                else hi = mid;
+              }
+              ent[k] = a.list_in[c_off[lo] + (e - c_pre[lo])];
             }
           }
-          if (count_it) {
-            ++my_regs;
-            register_slot(a, lg, slot);
+          uint32_t sym[kProbeBatch];
+          uint4 t[kProbeBatch];
+#pragma unroll
+          for (uint32_t k = 0; k < kProbeBatch; ++k) {
+            sym[k] = 0;
+            t[k] = make_uint4(0, 0, kEmpty32, 0);
+            const uint32_t w = (uint32_t)ent[k];
+            if (ent[k] == ~0ull || w >= W) continue;  // the last window of pass j-1 has no j-gram
+            const uint64_t pos = s0 + w + j - 1;
+            if (SB == 8) {
+              sym[k] = __ldg(a.data + pos);
+            } else {
+              sym[k] = (__ldg(a.data + (pos >> 2)) >> (6 - 2 * (pos & 3))) & 3u;
+            }
+            t[k] = __ldg(a.table + hash64_top(ent[k] >> 32, a.table_log2));
+          }
+#pragma unroll
+          for (uint32_t k = 0; k < kProbeBatch; ++k) {
+            const uint32_t w = (uint32_t)ent[k];
+            if (ent[k] == ~0ull || w >= W) continue;
+            const uint32_t id = probe_from(a.table, a.table_log2, ent[k] >> 32, t[k], a.ctl);
+            if (id == kEmpty32) continue;
+            const uint32_t slot = (id << SB) | sym[k];
+            ++my_surv;
+            if (a.list_out && s_out_base != ~0ull)
+              a.list_out[s_out_base + atomicAdd(&s_out_cnt, 1u)] = ((unsigned long long)slot << 32) | w;
+            bool count_it = true;
+            if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+              if (bm) {
+                count_it = bitmap_first(bm, slot);
+              } else {
+                const int rr = sset_try_insert(sset, slog, slot);
+                count_it = (rr == 1);
+                if (rr == 2) spill_push(spill_list, &s_nspill, slot);
+              }
+            }
+            if (count_it) {
+              ++my_regs;
+              register_slot(a, lg, slot);
+            }
           }
         }
         if (a.rlog) __syncthreads();

@@ -168,4 +168,18 @@ void launch_chain_keys(const uint32_t* sel_slot, const PassCtl* ctl, const uint3
   chain_keys_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, rank_prev, from_base, symbol_bits, keys_out);
 }
 
+namespace {
+__global__ void dmap_fill_kernel(const uint32_t* sel_slot, const PassCtl* ctl, const uint32_t* rank, uint32_t* dmap) {
+  const uint32_t n = ctl->nsel;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dmap[sel_slot[i]] = rank[i];
+}
+}  // namespace
+
+void launch_build_dmap(const uint32_t* sel_slot, const PassCtl* ctl, const uint32_t* rank, uint32_t* dmap,
+                       uint64_t entries, cudaStream_t s) {
+  cudaMemsetAsync(dmap, 0xFF, entries * sizeof(uint32_t), s);
+  dmap_fill_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, rank, dmap);
+}
+
 }  // namespace ig

@@ -103,6 +103,8 @@ def test_dna_reduced(mode):
     dict(threads=1024, words_per_thread=7, smem_set_log2=14, ctas_per_sm=1),
     dict(threads=512, words_per_thread=3, smem_set_log2=10, table_load_pct=50, hot_log2=6),
     dict(threads=512, words_per_thread=5, smem_set_log2=12, hot_log2=13),
+    dict(dense_prefix=1, words_per_thread=3),                                 # probe table in pass base + 1
+    dict(dense_prefix=2, threads=512),                                        # dense map in pass base + 1
 ])
 def test_results_do_not_depend_on_tuning(tuning):
     data, off, _ = synth.make_corpus("markov_2mb", seed=2)
