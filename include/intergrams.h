@@ -107,10 +107,14 @@ typedef struct {
                                 lists: 0 = auto (when the scan CTAs' bit vectors take at most
                                 48 MiB), 1 = never, 2 = whenever they fit in a quarter of the
                                 device memory */
-  uint32_t dense_prefix;     /* first candidate pass (j = base_n + 1): look the base-length prefix up
-                                in a dense map of sigma^base_n rows instead of the probe table:
-                                0 = auto (when the map and the counter array take at most
-                                112 MiB together, so both stay in L2), 1 = off, 2 = on */
+  uint32_t dense_prefix;     /* first candidate pass (j = base_n + 1), where every window is a
+                                candidate: 0 = auto (when a dense map of the sigma^base_n prefixes
+                                and the counter array take at most 112 MiB together, so both stay
+                                in L2, each thread rolls the key over its own run of windows and
+                                indexes the map; otherwise the queue path of the later passes with
+                                the probe table, which measured faster there), 1 = queue path
+                                always, 2 = runs with the dense map always, 3 = runs with the hot
+                                cache and probe table (slower; kept for comparison) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -194,11 +194,14 @@ uint32_t mode_of(const ig_plan* pl, uint32_t j) {
   return kModeShort;
 }
 
-// Pass j looks its prefixes up in the dense map (first candidate pass, not
-// followed by a chain pass, which needs survivor lists).
-bool dense_pass(const ig_plan* pl, uint32_t j) {
-  return pl->dmap && j == pl->b + 1 && mode_of(pl, j) == kModeShort && mode_of(pl, j + 1) != kModeChain;
+// Pass j is the first candidate pass run in per-thread window runs (it is
+// not followed by a chain pass, which needs survivor lists); with a dense
+// prefix map it looks prefixes up there.
+bool runs_pass(const ig_plan* pl, uint32_t j) {
+  return (pl->dmap || pl->t.dense_prefix == 3) && j == pl->b + 1 && mode_of(pl, j) == kModeShort &&
+         mode_of(pl, j + 1) != kModeChain;
 }
+bool dense_pass(const ig_plan* pl, uint32_t j) { return pl->dmap && runs_pass(pl, j); }
 
 // Kernels of one sort by count: init + (histogram, two scans, scatter) per 8-bit digit.
 uint32_t sort_kernels(const ig_plan* pl) { return 1 + 4 * (pl->narrow ? 2u : 4u); }
@@ -266,6 +269,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   }
   a.hot = pl->hot;
   a.hot_log2 = (md == kModeShort) ? pl->hot_log2 : 0u;
+  if (runs_pass(pl, j)) a.first_runs = 1;
   if (dense_pass(pl, j)) {
     a.dmap = pl->dmap;
     a.hot_log2 = 0;
@@ -522,7 +526,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
       t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13 || t.list_pct > 200 ||
-      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.dense_prefix > 2 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
+      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.dense_prefix > 3 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
       (t.log_range_log2 && (t.log_range_log2 < 10 || t.log_range_log2 > 30)))
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;

@@ -121,6 +121,7 @@ struct ScanArgs {
   // first candidate pass (j = base + 1, j * symbol_bits <= 32): counter row of
   // every base-length prefix, kEmpty32 = not a candidate; null = probe table
   const uint32_t* dmap;
+  uint32_t first_runs;         // pass base + 1 in per-thread window runs (no queue; no survivor lists)
   PassCtl* ctl;
 };
 

@@ -567,11 +567,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             }
           }
         }
-      } else if (a.dmap) {
-        // first candidate pass with a dense prefix map: every window is a
-        // candidate, so each thread rolls the key over its own run of
-        // windows as in the base pass; the (j-1)-gram prefix indexes the map
-        // directly (kProbeBatch map loads in flight per thread)
+      } else if (a.first_runs) {
+        // first candidate pass: every window is a candidate, so each thread
+        // rolls the key over its own run of windows as in the base pass; the
+        // (j-1)-gram prefix indexes the dense map, or goes to the hot cache
+        // and then the probe table (kProbeBatch loads in flight per thread)
         if (a.alive_out)
           for (uint32_t i = tid; i < alive_tile_words; i += nthr) tile_alive[i] = 0;
         __syncthreads();
@@ -597,21 +597,36 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             key = ((key << SB) | sym) & kmask;
           }
           for (uint32_t w = wb; w < we; w += kProbeBatch) {
-            uint32_t kk[kProbeBatch], rk[kProbeBatch];
+            uint32_t kk[kProbeBatch], rk[kProbeBatch], pend = 0;
+            uint4 e[kProbeBatch];
 #pragma unroll
             for (uint32_t k = 0; k < kProbeBatch; ++k) {
               rk[k] = kEmpty32;
               kk[k] = 0;
+              e[k] = make_uint4(0, 0, 0, 0);
               if (w + k < we) {
                 uint32_t sym;
                 IG_NEXT_SYM(sym);
                 key = ((key << SB) | sym) & kmask;
                 kk[k] = key;
-                rk[k] = __ldg(a.dmap + (key >> SB));
+                const uint32_t prefix = key >> SB;
+                if (a.dmap) {
+                  rk[k] = __ldg(a.dmap + prefix);
+                } else {
+                  if (H) {
+                    const uint32_t h = hash64_top(prefix, a.hot_log2);
+                    if (hot_keys[h] == prefix) rk[k] = hot_ids[h];
+                  }
+                  if (rk[k] == kEmpty32) {
+                    e[k] = __ldg(a.table + hash64_top(prefix, a.table_log2));
+                    pend |= 1u << k;
+                  }
+                }
               }
             }
 #pragma unroll
             for (uint32_t k = 0; k < kProbeBatch; ++k) {
+              if ((pend >> k) & 1u) rk[k] = probe_from(a.table, a.table_log2, kk[k] >> SB, e[k], a.ctl);
               if (rk[k] == kEmpty32) continue;
               const uint32_t slot = (rk[k] << SB) | (kk[k] & S::kMask);
               const uint32_t wt = w + k;

@@ -105,6 +105,7 @@ def test_dna_reduced(mode):
     dict(threads=512, words_per_thread=5, smem_set_log2=12, hot_log2=13),
     dict(dense_prefix=1, words_per_thread=3),                                 # probe table in pass base + 1
     dict(dense_prefix=2, threads=512),                                        # dense map in pass base + 1
+    dict(dense_prefix=3, hot_log2=7),                                         # window runs + probe table
 ])
 def test_results_do_not_depend_on_tuning(tuning):
     data, off, _ = synth.make_corpus("markov_2mb", seed=2)
