@@ -182,6 +182,33 @@ def cpu_baseline(name: str, seed: int, nseq: int, p):
     return {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample}, np
 
 
+def recall_leg(seed: int):
+    """Recall of the multi-pass top-k against the exhaustive top-k (both from
+    the CPU oracle) on the 2 MiB Markov workload at its full size (n = 4,
+    k = 1024, Z = 4096, base 1), and whether the GPU job returns the oracle's
+    Intergrams rows exactly."""
+    import numpy as np
+    import torch
+    from oracle import oracle
+    from paper_2511_14955_gb300 import binding, synth
+    w = synth.WORKLOADS["markov_2mb"]
+    data, off, _ = synth.make_corpus("markov_2mb", seed=seed)
+    ik, ic = oracle.intergrams(data, off, w.n, w.k, w.candidates, base_n=w.base_n)
+    ek, ec = oracle.exhaustive(data, off, w.n, w.k)
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(off.view(np.int64)).cuda()
+    with binding.Plan(d, o, n=w.n, k=w.k, candidates=w.candidates, base_n=w.base_n, graph=True) as pl:
+        pl.run()
+        gk, gc, _ = pl.topk()
+    ig = {bytes(r): int(c) for r, c in zip(ik, ic)}
+    ex = {bytes(r): int(c) for r, c in zip(ek, ec)}
+    inter = set(ig) & set(ex)
+    return {"workload": "markov_2mb (64 sequences, 2.2 MB), n=4 k=1024 Z=4096 base 1, Eq. 2",
+            "recall_at_k": len(inter) / max(1, len(ex)), "jaccard": len(inter) / max(1, len(set(ig) | set(ex))),
+            "counts_exact_on_common_rows": all(ig[x] == ex[x] for x in inter),
+            "gpu_equals_oracle": bool(np.array_equal(gk, ik) and np.array_equal(gc, ic))}
+
+
 def serving_leg(args, seed):
     """Poisson job stream (20 jobs/s; corpora of the 2 MiB workload's byte law,
     total sizes lognormal with median 64 MB, clamped to [1 MB, 512 MB] here to
@@ -358,6 +385,7 @@ def main(argv=None):
     if not args.no_cpu_baseline and world == 1:
         cb, _ = cpu_baseline(args.workload, seed, args.cpu_seqs, p)
         line["cpu_baseline"] = cb
+        line["recall"] = recall_leg(seed)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
