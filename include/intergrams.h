@@ -194,6 +194,29 @@ ig_status intergrams_rewind(ig_plan* pl);
 ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out,
                           uint32_t capacity, uint32_t* k_out, uint32_t* j_out);
 
+/*
+ * intergrams_features - the Boolean sequence x feature matrix the top-k
+ * n-grams are selected for (paper Sec. 1, Fig. 1): entry (i, f) is 1 exactly
+ * when sequence i contains the n-gram of row f of intergrams_topk after the
+ * last pass (Eq. 2 presence; the column sums are therefore the Eq. 2 counts
+ * of the rows). Runs two more scans of the corpus (a counting scan, then a
+ * writing scan) on the plan's stream and synchronises it.
+ *   row_ptr  : HOST uint64[m + 1], CSR row starts (row_ptr[0] = 0), or NULL.
+ *   cols     : HOST uint32[capacity], the feature ids of each row, ascending
+ *              and distinct, or NULL.
+ *   capacity : entries cols holds.
+ *   nnz_out  : receives the number of nonzeros (set whenever the matrix was
+ *              counted, also when capacity is too small).
+ * With both buffers NULL only nnz is computed; the count is kept until
+ * intergrams_rewind, so a second call with buffers sized nnz does not count
+ * again. Requires every pass to have run (IG_ESTATE otherwise), n * symbol_bits
+ * <= 64 and at most 2^20 rows (IG_EINVAL); capacity < nnz with cols given is
+ * IG_EINVAL (nothing written). Device scratch is allocated by the call and
+ * released by intergrams_free.
+ */
+ig_status intergrams_features(ig_plan* pl, uint64_t* row_ptr, uint32_t* cols, uint64_t capacity,
+                              uint64_t* nnz_out);
+
 /* Device bytes the plan allocated (or would allocate, for a plan made with IG_F_DRY_RUN). */
 ig_status intergrams_plan_device_bytes(const ig_plan* pl, uint64_t* bytes);
 

@@ -348,3 +348,69 @@ int oracle_count_keys(const uint8_t* data, const uint64_t* offsets, uint32_t m, 
   free(sorted); free(cnt); free(last); free(bitmap); free(win);
   return OR_OK;
 }
+
+/*
+ * The Boolean sequence x feature matrix that the top-k n-grams are chosen
+ * for (Sec. 1, Fig. 1): entry (i, f) is 1 exactly when sequence i contains
+ * the n-gram keys[f] (nkeys distinct rows of n symbol codes). Output in CSR
+ * form: row_ptr[m + 1] and, when capacity allows, cols with the f of each
+ * row in ascending order. *nnz_out is always set; OR_EINVAL if cols is too
+ * small (cols then holds the first capacity entries).
+ */
+static const uint8_t* g_feat_rows;
+static int cmp_feat_index(const void* a, const void* b) {
+  const uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+  return memcmp(g_feat_rows + (size_t)x * g_len, g_feat_rows + (size_t)y * g_len, g_len);
+}
+static int cmp_u32(const void* a, const void* b) {
+  const uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+  return x < y ? -1 : x > y;
+}
+
+int oracle_features(const uint8_t* data, const uint64_t* offsets, uint32_t m, uint32_t symbol_bits, uint32_t n,
+                    const uint8_t* keys, uint32_t nkeys, uint64_t* row_ptr, uint32_t* cols, uint64_t capacity,
+                    uint64_t* nnz_out) {
+  *nnz_out = 0;
+  if (n == 0 || !valid_corpus(offsets, m, symbol_bits)) return OR_EINVAL;
+  const size_t nk = nkeys ? nkeys : 1;
+  uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * nk);
+  uint8_t* sorted = (uint8_t*)malloc(nk * n);
+  uint8_t* present = (uint8_t*)calloc(nk, 1);
+  uint32_t* touched = (uint32_t*)malloc(sizeof(uint32_t) * nk);
+  uint8_t* win = (uint8_t*)malloc(n);
+  if (!order || !sorted || !present || !touched || !win) {
+    free(order); free(sorted); free(present); free(touched); free(win);
+    return OR_ENOMEM;
+  }
+  for (uint32_t f = 0; f < nkeys; ++f) order[f] = f;
+  g_len = n;
+  g_feat_rows = keys;
+  qsort(order, nkeys, sizeof(uint32_t), cmp_feat_index);
+  for (uint32_t i = 0; i < nkeys; ++i) memcpy(sorted + (size_t)i * n, keys + (size_t)order[i] * n, n);
+  uint64_t nnz = 0;
+  row_ptr[0] = 0;
+  for (uint32_t s = 0; s < m; ++s) {
+    const uint64_t a = offsets[s], L = offsets[s + 1] - a;
+    uint32_t nt = 0;
+    for (uint64_t p = a; L >= n && p + n <= a + L; ++p) {
+      for (uint32_t t = 0; t < n; ++t) win[t] = symbol_at(data, symbol_bits, p + t);
+      const uint8_t* hit = (const uint8_t*)bsearch(win, sorted, nkeys, n, cmp_key_row);
+      if (!hit) continue;
+      const uint32_t f = order[(uint64_t)(hit - sorted) / n];
+      if (!present[f]) {
+        present[f] = 1;
+        touched[nt++] = f;
+      }
+    }
+    qsort(touched, nt, sizeof(uint32_t), cmp_u32);
+    for (uint32_t t = 0; t < nt; ++t) {
+      if (nnz < capacity) cols[nnz] = touched[t];
+      ++nnz;
+      present[touched[t]] = 0;
+    }
+    row_ptr[s + 1] = nnz;
+  }
+  free(order); free(sorted); free(present); free(touched); free(win);
+  *nnz_out = nnz;
+  return nnz <= capacity ? OR_OK : OR_EINVAL;
+}

@@ -58,6 +58,8 @@ def _load():
         lib.oracle_intergrams.argtypes = [P, P, U32, U32, U32, U32, U64, U32, U64, U32, P, P, P, P]
         lib.oracle_count_keys.restype = ctypes.c_int
         lib.oracle_count_keys.argtypes = [P, P, U32, U32, U32, U32, P, U64, P]
+        lib.oracle_features.restype = ctypes.c_int
+        lib.oracle_features.argtypes = [P, P, U32, U32, U32, P, U32, P, P, U64, P]
         _lib = lib
     return _lib
 
@@ -126,3 +128,25 @@ def count_keys(data, offsets, keys, count_mode: int = EQ2_ONCE_PER_SEQUENCE, sym
     if rc != 0:
         raise ValueError(f"oracle_count_keys failed: {rc}")
     return out[:nk].copy()
+
+
+def features(data, offsets, keys, symbol_bits: int = 8):
+    """Boolean sequence x feature matrix (Sec. 1, Fig. 1) for the n-grams in
+    `keys` (rows of symbol codes, distinct): CSR (row_ptr uint64[m + 1],
+    cols uint32 ascending within each row)."""
+    lib = _load()
+    data, offsets, m = _prep(data, offsets)
+    keys = np.ascontiguousarray(np.asarray(keys, dtype=np.uint8))
+    nk, n = keys.shape
+    row_ptr = np.zeros(m + 1, np.uint64)
+    nnz = ctypes.c_uint64(0)
+    cap = 1 << 16
+    while True:
+        cols = np.zeros(cap, np.uint32)
+        rc = lib.oracle_features(data.ctypes.data, offsets.ctypes.data, m, symbol_bits, n, keys.ctypes.data, nk,
+                                 row_ptr.ctypes.data, cols.ctypes.data, cap, ctypes.byref(nnz))
+        if rc == 0:
+            return row_ptr, cols[: nnz.value].copy()
+        if nnz.value <= cap:
+            raise ValueError(f"oracle_features failed: {rc}")
+        cap = int(nnz.value)

@@ -29,7 +29,7 @@ EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_r
            "intergrams_stats", "intergrams_timings", "intergrams_free", "intergrams_last_error",
            "intergrams_dense_topk_static", "intergrams_plan_device_bytes", "intergrams_server_create",
            "intergrams_server_submit", "intergrams_server_wait", "intergrams_server_stats",
-           "intergrams_server_destroy", "intergrams_autotune"]
+           "intergrams_server_destroy", "intergrams_autotune", "intergrams_features"]
 
 
 class IgParams(ctypes.Structure):
@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
     lib.intergrams_topk.argtypes = [P, P, P, U32, ctypes.POINTER(U32), ctypes.POINTER(U32)]
     lib.intergrams_stats.restype = ctypes.c_int
     lib.intergrams_stats.argtypes = [P, ctypes.POINTER(IgPassStats)]
+    lib.intergrams_features.restype = ctypes.c_int
+    lib.intergrams_features.argtypes = [P, P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
     lib.intergrams_timings.restype = ctypes.c_int
     lib.intergrams_timings.argtypes = [P, P, P, U32, ctypes.POINTER(U32), ctypes.POINTER(U32)]
     lib.intergrams_free.restype = None
@@ -181,6 +183,7 @@ class Plan:
                                                     ctypes.byref(tun), ctypes.byref(self._h)),
                "intergrams_plan")
         self.n = n
+        self.m = m
         self.symbol_bits = symbol_bits
 
     def step(self):
@@ -208,6 +211,18 @@ class Plan:
         rb = (j * self.symbol_bits + 7) // 8
         flat = keys.reshape(-1)[: r * rb].reshape(r, rb) if r else np.zeros((0, rb), np.uint8)
         return flat.copy(), counts[:r].copy(), j
+
+    def features(self):
+        """(row_ptr, cols): the Boolean sequence x top-k matrix in CSR form
+        (uint64[m + 1] row starts, uint32 feature ids ascending per row)."""
+        nnz = ctypes.c_uint64(0)
+        _check(self._lib, self._lib.intergrams_features(self._h, None, None, 0, ctypes.byref(nnz)),
+               "intergrams_features")
+        row_ptr = np.zeros(self.m + 1, np.uint64)
+        cols = np.zeros(max(nnz.value, 1), np.uint32)
+        _check(self._lib, self._lib.intergrams_features(self._h, row_ptr.ctypes.data, cols.ctypes.data, nnz.value,
+                                                        ctypes.byref(nnz)), "intergrams_features")
+        return row_ptr, cols[: nnz.value].copy()
 
     def stats(self) -> dict:
         s = IgPassStats()

@@ -129,6 +129,16 @@ struct ig_plan {
   uint64_t bitmap_bits = 0;
   // dense prefix map of the first candidate pass (sigma^b rows)
   uint32_t* dmap = nullptr;
+  // feature matrix scratch (intergrams_features), kept until free; the count
+  // stays valid until rewind
+  unsigned long long* feat_keys = nullptr;
+  uint4* feat_table = nullptr;
+  uint32_t* feat_q = nullptr;  // two queue counters + status
+  uint32_t* feat_nnz = nullptr;
+  uint64_t* feat_rowptr = nullptr;
+  uint32_t feat_table_log2 = 0, feat_rows = 0;
+  bool feat_ready = false;
+  uint64_t feat_total = 0;
 };
 
 namespace {
@@ -169,7 +179,8 @@ void release(ig_plan* pl) {
                   pl->list_off[1], pl->list_cnt[0], pl->list_cnt[1], pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
                   pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank,
-                  pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap, pl->dmap};
+                  pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap, pl->dmap, pl->feat_keys,
+                  pl->feat_table, pl->feat_q, pl->feat_nnz, pl->feat_rowptr};
   for (void* q : ptrs)
     if (q) {
       if (pl->async_alloc) cudaFreeAsync(q, pl->stream);
@@ -798,6 +809,7 @@ ig_status intergrams_rewind(ig_plan* pl) {
   pl->last_j = 0;
   pl->nsel_last = 0;
   pl->kernels = 0;
+  pl->feat_ready = false;
   if ((pl->p.flags & IG_F_HOST_INPUT) && pl->data_bytes)
     IG_CUDA(cudaMemcpyAsync(pl->own_data, pl->host_data, pl->data_bytes, cudaMemcpyHostToDevice, pl->stream));
   return IG_OK;
@@ -827,6 +839,81 @@ ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out, 
     IG_CUDA(cudaMemcpyAsync(counts_out, pl->out_counts, (size_t)rows * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   IG_CUDA(cudaStreamSynchronize(s));
   *k_out = rows;
+  return IG_OK;
+}
+
+ig_status intergrams_features(ig_plan* pl, uint64_t* row_ptr, uint32_t* cols, uint64_t capacity, uint64_t* nnz_out) {
+  g_last_error.clear();
+  if (!pl || !nnz_out) return fail(IG_EINVAL, "plan or nnz_out is NULL");
+  *nnz_out = 0;
+  if (pl->dry_run) return fail(IG_ESTATE, "dry-run plan");
+  if (pl->last_j != pl->p.n || pl->next_j <= pl->p.n) return fail(IG_ESTATE, "the job's passes have not all run");
+  if (pl->p.n * pl->sb > 64) return fail(IG_EINVAL, "the feature matrix needs n * symbol_bits <= 64");
+  const uint32_t rows = std::min(pl->p.k, pl->nsel_last);
+  if (rows > (1u << 20)) return fail(IG_EINVAL, "the feature matrix takes at most 2^20 rows");
+  cudaStream_t s = pl->stream;
+  const uint32_t rb = row_bytes_for(pl, pl->p.n);
+  // feature scans: 1024 threads, the plan's words per thread, tile + halo
+  const uint32_t spw = 32 / pl->sb;
+  const uint64_t fwin = (uint64_t)pl->t.words_per_thread * spw * 1024;
+  const uint32_t ftile = (uint32_t)((((fwin + pl->p.n + 2 * 16 * (8 / pl->sb)) * pl->sb + 31) / 32 + 8 + 3) & ~3ull);
+  const size_t fsmem = feature_smem_bytes(std::max(rows, 1u), ftile);
+  int dev = 0, max_optin = 0;
+  IG_CUDA(cudaGetDevice(&dev));
+  IG_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (fsmem > (size_t)max_optin) return fail(IG_EINVAL, "feature bit vector and tile exceed shared memory");
+  if (!pl->feat_ready) {
+    if (rows) {  // the final rows on the device, as intergrams_topk writes them
+      launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->narrow ? 16u : 32u, pl->sidx[0], pl->sidx[1],
+                           pl->skey[0], pl->skey[1], pl->shist, s);
+      launch_write_topk(pl->sel_hist, pl->p.candidates, pl->b, pl->sel_count, pl->sidx[0], pl->ctl, pl->sb, pl->p.n,
+                        rb, rows, pl->out_keys, pl->out_counts, s);
+    }
+    if (!pl->feat_q) {
+      uint32_t tl = 8;
+      while ((1u << tl) < 4ull * std::max(pl->p.k, 1u)) ++tl;
+      pl->feat_table_log2 = tl;
+      IG_CUDA(cudaMalloc(&pl->feat_keys, sizeof(unsigned long long) * std::max(pl->p.k, 1u)));
+      IG_CUDA(cudaMalloc(&pl->feat_table, sizeof(uint4) << tl));
+      IG_CUDA(cudaMalloc(&pl->feat_q, 4 * sizeof(uint32_t)));
+      IG_CUDA(cudaMalloc(&pl->feat_nnz, sizeof(uint32_t) * std::max<uint32_t>(pl->m, 1)));
+      IG_CUDA(cudaMalloc(&pl->feat_rowptr, sizeof(uint64_t) * ((size_t)pl->m + 1)));
+    }
+    IG_CUDA(feature_set_smem(pl->sb, fsmem));
+    IG_CUDA(cudaMemsetAsync(pl->feat_q, 0, 4 * sizeof(uint32_t), s));
+    launch_features(pl->data, pl->data_bytes, pl->offsets, pl->d_order, pl->m, pl->p.n, pl->sb, pl->out_keys, rows, rb,
+                    pl->feat_keys, pl->feat_table, pl->feat_table_log2, pl->feat_q, pl->feat_q + 2, pl->feat_nnz,
+                    pl->feat_rowptr, nullptr, true, pl->sms, pl->t.words_per_thread, ftile, fsmem, s);
+    uint32_t st = 0;
+    IG_CUDA(cudaMemcpyAsync(&pl->feat_total, pl->feat_rowptr + pl->m, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    IG_CUDA(cudaMemcpyAsync(&st, pl->feat_q + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    IG_CUDA(cudaStreamSynchronize(s));
+    IG_CUDA(cudaGetLastError());
+    if (st) return fail(IG_ETABLE_FULL, "feature table full");
+    pl->feat_rows = rows;
+    pl->feat_ready = true;
+  }
+  *nnz_out = pl->feat_total;
+  if (cols && capacity < pl->feat_total) return fail(IG_EINVAL, "cols capacity is below the number of nonzeros");
+  if (cols && pl->feat_total) {
+    uint32_t* d_cols = nullptr;
+    IG_CUDA(cudaMalloc(&d_cols, sizeof(uint32_t) * pl->feat_total));
+    cudaError_t e = cudaMemsetAsync(pl->feat_q + 1, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) {
+      launch_features(pl->data, pl->data_bytes, pl->offsets, pl->d_order, pl->m, pl->p.n, pl->sb, pl->out_keys,
+                      pl->feat_rows, rb, pl->feat_keys, pl->feat_table, pl->feat_table_log2, pl->feat_q, pl->feat_q + 2,
+                      pl->feat_nnz, pl->feat_rowptr, d_cols, false, pl->sms, pl->t.words_per_thread, ftile, fsmem, s);
+      e = cudaMemcpyAsync(cols, d_cols, sizeof(uint32_t) * pl->feat_total, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaFree(d_cols);
+    if (e != cudaSuccess) return fail(IG_ECUDA, cudaGetErrorString(e));
+  }
+  if (row_ptr) {
+    IG_CUDA(cudaMemcpyAsync(row_ptr, pl->feat_rowptr, sizeof(uint64_t) * ((size_t)pl->m + 1), cudaMemcpyDeviceToHost, s));
+    IG_CUDA(cudaStreamSynchronize(s));
+  }
   return IG_OK;
 }
 

@@ -135,6 +135,15 @@ cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t sme
 cudaError_t chain_set_smem_limit(uint32_t symbol_bits, size_t smem);
 // Raise (never lower) the scan kernel's dynamic shared-memory limit to `smem`.
 cudaError_t scan_raise_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem);
+// Boolean sequence x feature matrix (ig_features.cu)
+size_t feature_smem_bytes(uint32_t nfeat, uint32_t tile_words);
+cudaError_t feature_set_smem(uint32_t sb, size_t smem);
+void launch_features(const uint8_t* data, uint64_t data_bytes, const uint64_t* offsets, const uint32_t* order,
+                     uint32_t m, uint32_t n, uint32_t sb, const uint8_t* rows, uint32_t nrows, uint32_t row_bytes,
+                     unsigned long long* keys, uint4* table, uint32_t table_log2, uint32_t* queue, uint32_t* status,
+                     uint32_t* row_nnz, uint64_t* row_ptr, uint32_t* cols, bool count, int grid,
+                     uint32_t words_per_thread, uint32_t tile_words, size_t smem, cudaStream_t s);
+
 // Count the registration log of the pass just scanned: one launch per counter
 // range, so the counters being incremented at any time span one range.
 void launch_log_count(const ScanArgs& a, cudaStream_t s);

@@ -104,3 +104,28 @@ def test_largen_full_size():
     check_properties(keys, counts, w.m)
     idx = sample_idx(len(counts), 24)
     assert np.array_equal(O.count_keys(data, off, keys[idx]), counts[idx])
+
+
+def test_malware_8gb_feature_matrix():
+    """Fig. 1's Boolean matrix of the 8.8 GB job: the column sums are the
+    top-k's Eq. 2 counts, rows are sorted and distinct, and sampled rows
+    equal the oracle's matrix of those sequences."""
+    w = synth.WORKLOADS["malware_8gb"]
+    data, off, bits = synth.make_corpus("malware_8gb")
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(off.view(np.int64)).cuda()
+    with B.Plan(d, o, n=w.n, k=w.k, candidates=w.candidates, base_n=w.base_n, graph=True, autotune=True) as pl:
+        pl.run()
+        keys, counts, _ = pl.topk()
+        row_ptr, cols = pl.features()
+    del d, o
+    torch.cuda.empty_cache()
+    assert row_ptr[0] == 0 and row_ptr[-1] == len(cols) and np.all(np.diff(row_ptr.astype(np.int64)) >= 0)
+    assert np.array_equal(np.bincount(cols, minlength=len(keys)), counts)
+    rng = np.random.default_rng(5)
+    for i in rng.choice(w.m, size=12, replace=False):
+        a, b = int(off[i]), int(off[i + 1])
+        row = cols[row_ptr[i]:row_ptr[i + 1]]
+        assert np.all(np.diff(row.astype(np.int64)) > 0)
+        er, ec = O.features(data[a:b], np.array([0, b - a], np.uint64), keys)
+        assert np.array_equal(row, ec), i

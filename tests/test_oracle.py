@@ -302,3 +302,43 @@ def test_count_keys_matches_exhaustive(mode, bits):
         got = O.count_keys(data, off, keys, mode, symbol_bits=bits)
         table = {bytes(k): int(c) for k, c in zip(ek, ec)}
         assert got.tolist() == [table.get(bytes(k), 0) for k in keys]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_features_match_brute_force(seed):
+    """Fig. 1's Boolean matrix: row i lists, ascending, the features whose
+    n-gram occurs in sequence i (sets of n-grams by brute force)."""
+    rng = np.random.default_rng(300 + seed)
+    sigma = [2, 3, 5, 256][seed % 4]
+    seqs = random_seqs(rng, int(rng.integers(1, 12)), 80, sigma)
+    data, off = corpus(seqs)
+    for n in (1, 2, 4):
+        allg = sorted(brute_counts(seqs, n, O.EQ2_ONCE_PER_SEQUENCE))
+        if not allg:
+            continue
+        pick = rng.choice(len(allg), size=min(len(allg), 1 + int(rng.integers(0, 30))), replace=False)
+        keys = np.array([allg[i] for i in pick], np.uint8).reshape(-1, n)
+        row_ptr, cols = O.features(data, off, keys)
+        assert row_ptr[0] == 0 and row_ptr[-1] == len(cols)
+        for i, s in enumerate(seqs):
+            present = {tuple(s[p:p + n]) for p in range(len(s) - n + 1)}
+            want = [f for f in range(len(keys)) if tuple(keys[f]) in present]
+            assert cols[row_ptr[i]:row_ptr[i + 1]].tolist() == want
+
+
+@pytest.mark.parametrize("bits", [8, 2])
+def test_feature_column_sums_are_eq2_counts(bits):
+    """Summing the matrix over sequences gives each feature's Eq. 2 count
+    (its number of sequences), here for the exhaustive top-k."""
+    rng = np.random.default_rng(77 + bits)
+    sigma = 4 if bits == 2 else 7
+    seqs = random_seqs(rng, 9, 400, sigma)
+    flat = [c for s in seqs for c in s]
+    data = _pack_by_hand(flat) if bits == 2 else np.asarray(flat, np.uint8)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([len(s) for s in seqs])
+    for n in (2, 5):
+        keys, counts = O.exhaustive(data, off, n, 60, O.EQ2_ONCE_PER_SEQUENCE, symbol_bits=bits)
+        row_ptr, cols = O.features(data, off, keys, symbol_bits=bits)
+        assert np.bincount(cols, minlength=len(keys)).tolist() == counts.tolist()
+        assert all(np.all(np.diff(cols[row_ptr[i]:row_ptr[i + 1]].astype(np.int64)) > 0) for i in range(len(seqs)))
