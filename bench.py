@@ -322,6 +322,17 @@ def main(argv=None):
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1)
     value, t_max = aggregate(elapsed, nbytes, npass, args.steps, world, reduce_max)
+    # the Boolean sequence x top-k matrix of the last job (two more corpus
+    # scans, CSR copied to the host), timed on its own after the timed region
+    features = None
+    if p["n"] * p["symbol_bits"] <= 64:
+        barrier()
+        t0 = time.perf_counter()
+        row_ptr, cols = plan.features()
+        dt = time.perf_counter() - t0
+        features = {"ms": dt * 1e3, "nnz": int(len(cols)), "rows": int(len(row_ptr) - 1),
+                    "scanned_gbps": 2 * nbytes / dt / 1e9,
+                    "note": "counting and writing scans of the corpus, CSR copied to host numpy arrays"}
     plan.close()
     del plan
 
@@ -380,6 +391,8 @@ def main(argv=None):
                      "peak_kind": f"{peak_kind} hbm_gbs", "avg_scan_ms": avg_scan_s * 1e3},
         "clocks": clk,
     }
+    if features:
+        line["features"] = features
     if args.serve_jobs and world == 1:
         line["serving"] = serving_leg(args, seed)
     if not args.no_cpu_baseline and world == 1:

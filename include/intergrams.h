@@ -115,6 +115,9 @@ typedef struct {
                                 the probe table, which measured faster there), 1 = queue path
                                 always, 2 = runs with the dense map always, 3 = runs with the hot
                                 cache and probe table (slower; kept for comparison) */
+  uint32_t base_words_per_thread; /* the dense base pass's own words_per_thread and smem_set_log2 */
+  uint32_t base_smem_set_log2;    /* (0 = the values above); it needs no queue or hot cache, so a */
+                                  /* larger set fits beside a larger tile */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

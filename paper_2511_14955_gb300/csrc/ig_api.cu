@@ -102,6 +102,9 @@ struct ig_plan {
   int scan_grid = 0, scan_threads = 512;
   size_t scan_smem = 0;
   uint32_t tile_words = 0;
+  // the dense base pass's own tile and set (no queue, no hot cache)
+  uint32_t base_wpt = 0, base_sset_log2 = 0, base_tile_words = 0;
+  size_t base_smem = 0;
   uint32_t queue_words = 0;
 
   uint8_t* out_keys = nullptr;
@@ -258,6 +261,12 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.queue_words = pl->queue_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
   a.narrow = pl->narrow ? 1u : 0u;
+  if (base) {  // the base pass's own tile and set; no queue
+    a.words_per_thread = pl->base_wpt;
+    a.sset_log2 = pl->base_sset_log2;
+    a.tile_words = pl->base_tile_words;
+    a.queue_words = 0;
+  }
   a.tile_base = pl->d_tile_base;
   a.tile_windows = pl->tile_windows;
   a.runs_per_tile = pl->runs_per_tile;
@@ -302,7 +311,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   if (timing) cudaEventRecordWithFlags(pl->ev_scan0[ti], s, evf);
   if (pl->m > 0) {
     if (md == kModeChain) launch_chain(a, pl->sb, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
-    else launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, pl->scan_smem, s);
+    else launch_scan(a, pl->sb, base, pl->scan_grid, pl->scan_threads, base ? pl->base_smem : pl->scan_smem, s);
     kernels += 1;
     if (a.rlog) {
       launch_log_count(a, s);
@@ -586,12 +595,27 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   pl->t = t;
   pl->scan_threads = (int)t.threads;
   pl->scan_smem = smem_for(t.smem_set_log2);
-  for (bool base : {true, false}) PLAN_CUDA(scan_set_smem_limit(pl->sb, base, pl->scan_smem));
+  // the base pass: its own words per thread and set size; shared memory =
+  // set + tile only
+  pl->base_wpt = t.base_words_per_thread ? t.base_words_per_thread : t.words_per_thread;
+  pl->base_sset_log2 = t.base_smem_set_log2 ? t.base_smem_set_log2 : t.smem_set_log2;
+  if (!(pl->base_wpt & 1u) || pl->base_wpt > 31 || pl->base_sset_log2 < 8 || pl->base_sset_log2 > 15 ||
+      (uint64_t)pl->base_wpt * spw * t.threads > 65536)
+    return bail(fail(IG_EINVAL, "base-pass tuning knob out of range"));
+  {
+    const uint64_t bw = (uint64_t)pl->base_wpt * spw * t.threads;
+    pl->base_tile_words = (uint32_t)((((bw + p->n + 2 * 16 * (8 / pl->sb)) * pl->sb + 31) / 32 + 8 + 3) & ~3ull);
+    pl->base_smem = ((size_t)4 << pl->base_sset_log2) + (size_t)4 * pl->base_tile_words;
+    if (pl->base_smem + 256 > (size_t)max_optin)
+      return bail(fail(IG_EINVAL, "base-pass tuning needs more shared memory than a CTA can have"));
+  }
+  PLAN_CUDA(scan_set_smem_limit(pl->sb, true, pl->base_smem));
+  PLAN_CUDA(scan_set_smem_limit(pl->sb, false, pl->scan_smem));
   PLAN_CUDA(chain_set_smem_limit(pl->sb, pl->scan_smem));
   pl->tile_windows = (uint32_t)tile_windows;
   pl->runs_per_tile = (uint32_t)((tile_windows + kRunChunk - 1) / kRunChunk);
   int occ = std::min(scan_max_ctas_per_sm(pl->sb, false, pl->scan_threads, pl->scan_smem),
-                     scan_max_ctas_per_sm(pl->sb, true, pl->scan_threads, pl->scan_smem));
+                     scan_max_ctas_per_sm(pl->sb, true, pl->scan_threads, pl->base_smem));
   if (occ < 1) return bail(fail(IG_EINVAL, "scan kernel does not fit on an SM with these tuning knobs"));
   pl->scan_grid = pl->sms * (int)std::min<uint32_t>(t.ctas_per_sm, (uint32_t)occ);
 

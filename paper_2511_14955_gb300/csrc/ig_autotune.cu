@@ -4,7 +4,9 @@
 // The sample is a prefix of the sequences (sequences are independent, so a
 // prefix is a fair sample of an i.i.d. corpus) of about sample_bytes. Each
 // candidate runs the whole job on the sample with per-pass CUDA-event timing;
-// the fastest total wins. Every candidate must return byte-identical top-k
+// the candidate with the fastest candidate passes wins, and the dense base
+// pass takes the tile and set size of the candidate (same CTA shape) with the
+// fastest base pass. Every candidate must return byte-identical top-k
 // rows and counts (the knobs only change speed and memory); a mismatch is
 // reported as IG_ESTATE. Choices are cached in-process per (device, alphabet,
 // n, base, candidate-count bucket, count mode, corpus-size bucket).
@@ -13,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "ig_internal.cuh"
@@ -89,12 +92,13 @@ extern "C" ig_status intergrams_autotune(const ig_params* p, const void* data, c
   float best = 1e30f;
   ig_tuning best_t = kCandidates[0];
   bool have_ref = false;
+  std::vector<std::pair<ig_tuning, float>> base_times;  // base-pass ms of every candidate that ran
   for (const ig_tuning& cand : kCandidates) {
     ig_plan* pl = nullptr;
     ig_status st = intergrams_plan(&sp, sdata, h.data(), ms, stream, &cand, &pl);
     if (st == IG_EINVAL || st == IG_ENOMEM) continue;  // does not fit this device or corpus
     if (st != IG_OK) return st;
-    float total = 0.f;
+    float total = 0.f, base_ms = 0.f;
     for (int rep = 0; rep < 2 && st == IG_OK; ++rep) {  // first run warms caches and the pool
       intergrams_rewind(pl);
       st = intergrams_run(pl);
@@ -103,7 +107,9 @@ extern "C" ig_status intergrams_autotune(const ig_params* p, const void* data, c
       uint32_t np = 0;
       st = intergrams_timings(pl, nullptr, pass.data(), (uint32_t)pass.size(), &np, nullptr);
       total = 0.f;
-      for (uint32_t i = 0; i < np; ++i) total += pass[i];
+      base_ms = np ? pass[0] : 0.f;  // pass[0] is the dense base pass
+      for (uint32_t i = 1; i < np; ++i) total += pass[i];
+      if (np == 1) total = base_ms;  // n == base_n: the base pass is the whole job
     }
     if (st == IG_OK) {
       keys.assign((size_t)p->k * rb, 0);
@@ -124,10 +130,20 @@ extern "C" ig_status intergrams_autotune(const ig_params* p, const void* data, c
       ig::set_last_error("autotune: tuning candidates disagree on the result");
       return IG_ESTATE;
     }
+    base_times.emplace_back(cand, base_ms);
     if (total < best) {
       best = total;
       best_t = cand;
     }
+  }
+  {
+    float bb = 1e30f;
+    for (const auto& bt : base_times)
+      if (bt.first.ctas_per_sm == best_t.ctas_per_sm && bt.first.threads == best_t.threads && bt.second < bb) {
+        bb = bt.second;
+        best_t.base_words_per_thread = bt.first.words_per_thread;
+        best_t.base_smem_set_log2 = bt.first.smem_set_log2;
+      }
   }
   if (!have_ref) {
     ig::set_last_error("autotune: no candidate could run");
