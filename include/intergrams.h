@@ -118,6 +118,8 @@ typedef struct {
   uint32_t base_words_per_thread; /* the dense base pass's own words_per_thread and smem_set_log2 */
   uint32_t base_smem_set_log2;    /* (0 = the values above); it needs no queue or hot cache, so a */
                                   /* larger set fits beside a larger tile */
+  uint32_t set_probes;       /* Eq. 2: positions a slot may take in the shared-memory set before it
+                                goes to the spill list (1..8; default 2, measured fastest) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

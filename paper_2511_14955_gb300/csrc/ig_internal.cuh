@@ -122,6 +122,7 @@ struct ScanArgs {
   // every base-length prefix, kEmpty32 = not a candidate; null = probe table
   const uint32_t* dmap;
   uint32_t first_runs;         // pass base + 1 in per-thread window runs (no queue; no survivor lists)
+  uint32_t set_probes;         // bounded probe length of the shared-memory dedupe set (1..8)
   PassCtl* ctl;
 };
 

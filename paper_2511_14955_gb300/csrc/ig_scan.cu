@@ -128,6 +128,15 @@ __device__ __forceinline__ uint64_t tile_key(const uint32_t* tile, uint32_t o, u
   return bits >= 64 ? v : (v >> (64 - bits));
 }
 
+// tile_key for keys of at most 32 bits (two words).
+template <int SB>
+__device__ __forceinline__ uint64_t tile_key32(const uint32_t* tile, uint32_t o, uint32_t j) {
+  const uint32_t bit = o * SB, wi = bit >> 5, sh = bit & 31;
+  const uint32_t v = __funnelshift_l(__byte_perm(tile[wi + 1], 0, 0x0123), __byte_perm(tile[wi], 0, 0x0123), sh);
+  const uint32_t bits = j * SB;
+  return bits >= 32 ? v : (v >> (32 - bits));
+}
+
 // Symbol `o` of the tile.
 template <int SB>
 __device__ __forceinline__ uint32_t tile_sym(const uint32_t* tile, uint32_t o) {
@@ -142,10 +151,10 @@ __device__ __forceinline__ uint32_t tile_sym(const uint32_t* tile, uint32_t o) {
 // once found its path full finds it full forever (entries are never removed
 // within a sequence), so the spilled slots and the slots in the set are
 // disjoint.
-__device__ __forceinline__ int sset_try_insert(uint32_t* sset, uint32_t slog, uint32_t slot) {
+__device__ __forceinline__ int sset_try_insert(uint32_t* sset, uint32_t slog, uint32_t slot, uint32_t probes) {
   const uint32_t mask = (1u << slog) - 1u;
   uint32_t h = hash32_top(slot, slog);
-  const uint32_t maxp = mask < 3u ? mask + 1u : 4u;
+  const uint32_t maxp = mask < probes - 1u ? mask + 1u : probes;
   for (uint32_t p = 0; p < maxp; ++p) {
     uint32_t cur = sset[h];
     if (cur == slot) return 0;
@@ -554,7 +563,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
-                const int r = sset_try_insert(sset, slog, slot);
+                const int r = sset_try_insert(sset, slog, slot, a.set_probes);
                 count_it = (r == 1);
                 if (r == 2) spill_push(spill_list, &s_nspill, slot);
               } else {
@@ -637,7 +646,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
                 if (bm) {
                   count_it = bitmap_first(bm, slot);
                 } else if (spill_list) {
-                  const int r = sset_try_insert(sset, slog, slot);
+                  const int r = sset_try_insert(sset, slog, slot, a.set_probes);
                   count_it = (r == 1);
                   if (r == 2) spill_push(spill_list, &s_nspill, slot);
                 } else {
@@ -743,6 +752,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
         }
         // kProbeBatch queued windows per thread per round: the probe-table
         // loads of a round's hot-cache misses are all issued before any is used
+        const bool short_key = (j - 1) * SB <= 32;
         for (uint32_t qb = q0 + tid; qb < q1; qb += kProbeBatch * nthr) {
           uint64_t prefix[kProbeBatch];
           uint32_t wl[kProbeBatch], id[kProbeBatch];
@@ -753,18 +763,19 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             id[k] = kEmpty32;
             wl[k] = 0xFFFFFFFFu;  // not a window
             prefix[k] = 0;
+            uint64_t hp = 0;  // one multiply-shift product for the hot cache and the table
             if (qi < q1) {
               const uint32_t w = queue[qi];
-              prefix[k] = tile_key<SB>(tile, sym_off + w, j - 1);
+              prefix[k] = short_key ? tile_key32<SB>(tile, sym_off + w, j - 1) : tile_key<SB>(tile, sym_off + w, j - 1);
               wl[k] = (w << 8) | tile_sym<SB>(tile, sym_off + w + j - 1);
+              hp = prefix[k] * 0x9E3779B97F4A7C15ull;
               if (H) {
-                const uint32_t h = hash64_top(prefix[k], a.hot_log2);
+                const uint32_t h = (uint32_t)(hp >> (64 - a.hot_log2));
                 if (hot_keys[h] == prefix[k]) id[k] = hot_ids[h];
               }
             }
             e[k] = make_uint4(0, 0, 0, 0);
-            if (wl[k] != 0xFFFFFFFFu && id[k] == kEmpty32)
-              e[k] = __ldg(a.table + hash64_top(prefix[k], a.table_log2));
+            if (wl[k] != 0xFFFFFFFFu && id[k] == kEmpty32) e[k] = __ldg(a.table + (uint32_t)(hp >> (64 - a.table_log2)));
           }
 #pragma unroll
           for (uint32_t k = 0; k < kProbeBatch; ++k) {
@@ -787,7 +798,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
-                const int r = sset_try_insert(sset, slog, slot);
+                const int r = sset_try_insert(sset, slog, slot, a.set_probes);
                 count_it = (r == 1);
                 if (r == 2) spill_push(spill_list, &s_nspill, slot);
               } else {
@@ -993,7 +1004,7 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else {
-                const int rr = sset_try_insert(sset, slog, slot);
+                const int rr = sset_try_insert(sset, slog, slot, a.set_probes);
                 count_it = (rr == 1);
                 if (rr == 2) spill_push(spill_list, &s_nspill, slot);
               }
