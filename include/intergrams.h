@@ -120,6 +120,9 @@ typedef struct {
                                   /* larger set fits beside a larger tile */
   uint32_t set_probes;       /* Eq. 2: positions a slot may take in the shared-memory set before it
                                 goes to the spill list (1..8; default 2, measured fastest) */
+  uint32_t tile_buffers;     /* corpus tiles staged by bulk copy into 2 shared-memory buffers (the
+                                next tile's copy overlaps this tile's work) when both fit, else 1;
+                                1 forces one buffer (0 = default 2) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

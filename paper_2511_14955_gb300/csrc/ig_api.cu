@@ -105,6 +105,7 @@ struct ig_plan {
   // the dense base pass's own tile and set (no queue, no hot cache)
   uint32_t base_wpt = 0, base_sset_log2 = 0, base_tile_words = 0;
   size_t base_smem = 0;
+  uint32_t tile2 = 0, base_tile2 = 0;  // word offsets of the second tile buffers (0 = one buffer)
   uint32_t queue_words = 0;
 
   uint8_t* out_keys = nullptr;
@@ -262,11 +263,13 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.check_overflow = pl->check_overflow ? 1u : 0u;
   a.narrow = pl->narrow ? 1u : 0u;
   a.set_probes = pl->t.set_probes ? pl->t.set_probes : 2u;
+  a.tile2 = pl->tile2;
   if (base) {  // the base pass's own tile and set; no queue
     a.words_per_thread = pl->base_wpt;
     a.sset_log2 = pl->base_sset_log2;
     a.tile_words = pl->base_tile_words;
     a.queue_words = 0;
+    a.tile2 = pl->base_tile2;
   }
   a.tile_base = pl->d_tile_base;
   a.tile_windows = pl->tile_windows;
@@ -370,6 +373,7 @@ ig_status read_status(ig_plan* pl) {
   pl->nsel_last = pl->h_ctl->nsel;
   if (st & kStCountOverflow) return fail(IG_EOVERFLOW, "a 32-bit count overflowed");
   if (st & kStListFull) return fail(IG_ETABLE_FULL, "a survivor list exceeded its capacity (raise list_pct)");
+  if (st & kStTimeout) return fail(IG_ETIMEOUT, "a tile's bulk copy did not complete");
   if (st & (kStSetFull | kStTableFull)) return fail(IG_ETABLE_FULL, "a device hash table filled up");
   if (st) return fail(IG_ECUDA, "device status error");
   return IG_OK;
@@ -403,6 +407,7 @@ ig_status plan_last_status(ig_plan* pl) {
   pl->nsel_last = pl->h_ctl->nsel;
   if (st & kStCountOverflow) return fail(IG_EOVERFLOW, "a 32-bit count overflowed");
   if (st & kStListFull) return fail(IG_ETABLE_FULL, "a survivor list exceeded its capacity (raise list_pct)");
+  if (st & kStTimeout) return fail(IG_ETIMEOUT, "a tile's bulk copy did not complete");
   if (st & (kStSetFull | kStTableFull)) return fail(IG_ETABLE_FULL, "a device hash table filled up");
   if (st) return fail(IG_ECUDA, "device status error");
   return IG_OK;
@@ -547,7 +552,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
       t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13 || t.list_pct > 200 ||
-      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.set_probes > 8 || t.dense_prefix > 3 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
+      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.set_probes > 8 || t.tile_buffers > 2 || t.dense_prefix > 3 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
       (t.log_range_log2 && (t.log_range_log2 < 10 || t.log_range_log2 > 30)))
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;
@@ -609,6 +614,18 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
     pl->base_smem = ((size_t)4 << pl->base_sset_log2) + (size_t)4 * pl->base_tile_words;
     if (pl->base_smem + 256 > (size_t)max_optin)
       return bail(fail(IG_EINVAL, "base-pass tuning needs more shared memory than a CTA can have"));
+  }
+  // second tile buffers, where they fit (with room for the kernels' static
+  // shared memory)
+  if (t.tile_buffers != 1) {
+    if (pl->scan_smem + (size_t)4 * pl->tile_words + 2048 <= (size_t)max_optin) {
+      pl->tile2 = (uint32_t)(pl->scan_smem / 4);
+      pl->scan_smem += (size_t)4 * pl->tile_words;
+    }
+    if (pl->base_smem + (size_t)4 * pl->base_tile_words + 2048 <= (size_t)max_optin) {
+      pl->base_tile2 = (uint32_t)(pl->base_smem / 4);
+      pl->base_smem += (size_t)4 * pl->base_tile_words;
+    }
   }
   PLAN_CUDA(scan_set_smem_limit(pl->sb, true, pl->base_smem));
   PLAN_CUDA(scan_set_smem_limit(pl->sb, false, pl->scan_smem));

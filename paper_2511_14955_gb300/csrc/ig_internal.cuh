@@ -32,6 +32,7 @@ enum : uint32_t {
   kStCountOverflow = 1u << 2,  // a 32-bit count wrapped (Eq. 1 only)
   kStQueue = 1u << 3,          // work queue inconsistency
   kStListFull = 1u << 4,       // a survivor list ran out of its capacity
+  kStTimeout = 1u << 5,        // a bounded wait for a tile's bulk copy ran out
 };
 
 // Device-side control block, one per plan. The pass fields are zeroed at the
@@ -123,6 +124,7 @@ struct ScanArgs {
   const uint32_t* dmap;
   uint32_t first_runs;         // pass base + 1 in per-thread window runs (no queue; no survivor lists)
   uint32_t set_probes;         // bounded probe length of the shared-memory dedupe set (1..8)
+  uint32_t tile2;              // word offset of the second tile buffer in dynamic smem (0 = one buffer)
   PassCtl* ctl;
 };
 

@@ -128,6 +128,90 @@ __device__ __forceinline__ uint64_t tile_key(const uint32_t* tile, uint32_t o, u
   return bits >= 64 ? v : (v >> (64 - bits));
 }
 
+// ---- tile staging with the bulk-copy engine --------------------------------
+// A tile's bytes [al, al + nbytes) (al 16-byte aligned, nbytes a multiple of
+// 16) go to shared memory by one cp.async.bulk for the part inside the
+// corpus' 16-byte aligned extent, completing on an mbarrier; the few 16-byte
+// chunks outside it (only at the corpus' ends) are built with byte loads,
+// zero past the corpus.
+struct TileGeom {
+  uint32_t nwin, sym_off, nbytes;
+  uint64_t gsym;
+  uintptr_t al;
+};
+
+template <int SB>
+__device__ __forceinline__ TileGeom tile_geom(const ScanArgs& a, uint64_t s0, uint64_t W, uint64_t w0,
+                                              uint32_t tile_windows, uint32_t j) {
+  TileGeom g;
+  g.nwin = (uint32_t)((W - w0) < tile_windows ? (W - w0) : tile_windows);
+  g.gsym = s0 + w0;
+  const uint64_t nsym = (uint64_t)g.nwin + j - 1;
+  const uint64_t b_first = (g.gsym * SB) >> 3;
+  const uint64_t b_end = ((g.gsym + nsym) * SB + 7) >> 3;
+  const uintptr_t addr_first = reinterpret_cast<uintptr_t>(a.data) + b_first;
+  g.al = addr_first & ~(uintptr_t)15;
+  g.sym_off = (uint32_t)(addr_first - g.al) * (32 / SB) / 4u + (uint32_t)(g.gsym % (8u / SB));
+  g.nbytes = (uint32_t)((reinterpret_cast<uintptr_t>(a.data) + b_end - g.al + 15) & ~(uintptr_t)15);
+  return g;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_addr(bar);
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Start staging tile `g` into `buf` (all threads call; thread 0 issues the
+// bulk copy and arms the barrier, the others build the edge chunks).
+__device__ __forceinline__ void stage_issue(const ScanArgs& a, const TileGeom& g, uint8_t* buf, uint64_t* bar) {
+  const uintptr_t lo_ok = reinterpret_cast<uintptr_t>(a.data), hi_ok = lo_ok + a.data_bytes;
+  const uintptr_t lo16 = (lo_ok + 15) & ~(uintptr_t)15, hi16 = hi_ok & ~(uintptr_t)15;
+  const uintptr_t ia = g.al > lo16 ? g.al : lo16;
+  const uintptr_t ie = (g.al + g.nbytes) < hi16 ? (g.al + g.nbytes) : hi16;
+  const uint32_t bytes = ie > ia ? (uint32_t)(ie - ia) : 0u;
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    if (bytes)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_addr(buf + (ia - g.al))),
+          "l"(ia), "r"(bytes), "r"(smem_addr(bar))
+          : "memory");
+  }
+  for (uint32_t x = threadIdx.x * 16u; x < g.nbytes; x += blockDim.x * 16u) {
+    const uintptr_t p = g.al + x;
+    if (bytes && p >= ia && p < ie) continue;  // part of the bulk copy
+    uint32_t w[4] = {0, 0, 0, 0};
+    for (int b = 0; b < 16; ++b) {
+      const uintptr_t q = p + b;
+      const uint32_t byte = (q >= lo_ok && q < hi_ok) ? *reinterpret_cast<const uint8_t*>(q) : 0u;
+      w[b >> 2] |= byte << (8 * (b & 3));
+    }
+    *reinterpret_cast<uint4*>(buf + x) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 // tile_key for keys of at most 32 bits (two words).
 template <int SB>
 __device__ __forceinline__ uint64_t tile_key32(const uint32_t* tile, uint32_t o, uint32_t j) {
@@ -453,12 +537,19 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   uint32_t* sset = smem;
   unsigned long long* hot_keys = reinterpret_cast<unsigned long long*>(smem + (1u << a.sset_log2));
   uint32_t* hot_ids = reinterpret_cast<uint32_t*>(hot_keys + H);
-  uint32_t* tile = hot_ids + H;
-  uint8_t* tile_b = reinterpret_cast<uint8_t*>(tile);
+  uint32_t* tile0 = hot_ids + H;
   // candidate passes: queue of alive windows (tile-relative indices) and the
-  // tile's survivor bits
-  uint16_t* queue = reinterpret_cast<uint16_t*>(tile + a.tile_words);
-  uint32_t* tile_alive = tile + a.tile_words + a.queue_words;
+  // tile's survivor bits; a second tile buffer at word a.tile2 (0 = none)
+  // lets the next tile's bulk copy run while this one is processed
+  uint16_t* queue = reinterpret_cast<uint16_t*>(tile0 + a.tile_words);
+  uint32_t* tile_alive = tile0 + a.tile_words + a.queue_words;
+  uint32_t* const tile1 = a.tile2 ? smem + a.tile2 : tile0;
+  __shared__ __align__(8) uint64_t s_bar[2];
+  if (tid == 0) {
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+  }
+  uint32_t bar_phases = 0;  // bit b: phase parity of barrier b
   const uint32_t alive_tile_words = (tile_windows + 31) / 32;
   unsigned long long* gset = a.gset ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
   uint32_t* bm = a.bitmap ? a.bitmap + (uint64_t)blockIdx.x * a.bitmap_words : nullptr;
@@ -505,38 +596,23 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     }
     if (tid == 0) s_nspill = 0;
 
-    for (uint64_t w0 = 0; w0 < W; w0 += tile_windows) {
-      const uint32_t nwin = (uint32_t)((W - w0) < tile_windows ? (W - w0) : tile_windows);
-      const uint64_t gsym = s0 + w0;                     // first symbol of the tile
-      const uint64_t nsym = (uint64_t)nwin + j - 1;      // symbols the tile needs
-      const uint64_t b_first = (gsym * SB) >> 3;
-      const uint64_t b_end = ((gsym + nsym) * SB + 7) >> 3;
-      const uintptr_t addr_first = reinterpret_cast<uintptr_t>(a.data) + b_first;
-      const uintptr_t al = addr_first & ~(uintptr_t)15;
-      const uint32_t sym_off = (uint32_t)(addr_first - al) * S::kPerWord / 4u +
-                               (uint32_t)(gsym % (8u / SB));
-      const uint32_t nbytes = (uint32_t)((reinterpret_cast<uintptr_t>(a.data) + b_end - al + 15) & ~(uintptr_t)15);
-      const uintptr_t lo_ok = reinterpret_cast<uintptr_t>(a.data);
-      const uintptr_t hi_ok = lo_ok + a.data_bytes;
-      // stage the tile (+ halo) in shared memory; 16-byte vector loads where
-      // the whole vector lies inside the corpus, byte loads at the edges
-      for (uint32_t x = tid * 16u; x < nbytes; x += nthr * 16u) {
-        const uintptr_t p = al + x;
-        uint4 v;
-        if (p >= lo_ok && p + 16 <= hi_ok) {
-          v = __ldcs(reinterpret_cast<const uint4*>(p));
-        } else {
-          uint32_t w[4] = {0, 0, 0, 0};
-          for (int b = 0; b < 16; ++b) {
-            uintptr_t q = p + b;
-            uint32_t byte = (q >= lo_ok && q < hi_ok) ? *reinterpret_cast<const uint8_t*>(q) : 0u;
-            w[b >> 2] |= byte << (8 * (b & 3));
-          }
-          v = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        *reinterpret_cast<uint4*>(tile_b + x) = v;
-      }
-      __syncthreads();
+    // tile t of the sequence is in buffer t & 1 (always buffer 0 without a
+    // second buffer); tile 0 is issued here, tile t + 1 once tile t arrived
+    __syncthreads();  // the previous sequence is done with both buffers
+    stage_issue(a, tile_geom<SB>(a, s0, W, 0, tile_windows, j), reinterpret_cast<uint8_t*>(tile0), &s_bar[0]);
+    uint32_t tix = 0;
+    for (uint64_t w0 = 0; w0 < W; w0 += tile_windows, ++tix) {
+      const TileGeom g = tile_geom<SB>(a, s0, W, w0, tile_windows, j);
+      const uint32_t nwin = g.nwin, sym_off = g.sym_off;
+      const uint64_t gsym = g.gsym;
+      const uint32_t bsel = a.tile2 ? (tix & 1u) : 0u;
+      uint32_t* tile = bsel ? tile1 : tile0;
+      if (!mbar_wait(s_bar + bsel, (bar_phases >> bsel) & 1u)) atomicOr(&a.ctl->status, kStTimeout);
+      bar_phases ^= 1u << bsel;
+      __syncthreads();  // edge chunks written by other threads are visible
+      if (a.tile2 && w0 + tile_windows < W)
+        stage_issue(a, tile_geom<SB>(a, s0, W, w0 + tile_windows, tile_windows, j),
+                    reinterpret_cast<uint8_t*>(bsel ? tile0 : tile1), s_bar + (bsel ^ 1u));
 
       const uint32_t wb = tid * R;
       if (BASE) {
@@ -836,10 +912,13 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
         }
       }
       __syncthreads();
+      if (!a.tile2 && w0 + tile_windows < W)  // one buffer: stage the next tile now
+        stage_issue(a, tile_geom<SB>(a, s0, W, w0 + tile_windows, tile_windows, j),
+                    reinterpret_cast<uint8_t*>(tile0), &s_bar[0]);
     }
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       const uint32_t nsp = s_nspill;  // read after the tile loop's final barrier
-      if (nsp) dedupe_spills(a, lg, nsp, sset, tile, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
+      if (nsp) dedupe_spills(a, lg, nsp, sset, tile0, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
       __syncthreads();
     }
   }
