@@ -220,9 +220,15 @@ def serving_leg(args, seed):
     tun = {"list_pct": 50}
     batched = serving.run_stream(pool, jobs, max_active=8, tuning=tun)
     single = serving.run_stream(pool, jobs, max_active=1, tuning=tun)
-    return {"workload": f"{len(jobs)} Poisson jobs at {args.serve_rate:g}/s over {len(pool)} corpora "
-                        f"({sum(int(o[-1]) for _, o in pool) / 1e6:.0f} MB), n in {{4,8,16}}, k in {{1K,16K,256K}}",
-            "continuous_batching": batched, "one_job_per_launch": single}
+    out = {"workload": f"{len(jobs)} Poisson jobs at {args.serve_rate:g}/s over {len(pool)} corpora "
+                       f"({sum(int(o[-1]) for _, o in pool) / 1e6:.0f} MB), n in {{4,8,16}}, k in {{1K,16K,256K}}",
+           "continuous_batching": batched, "one_job_per_launch": single}
+    # the same job mix at four times the arrival rate, where jobs overlap
+    hot = serving.job_stream(args.serve_jobs, 4 * args.serve_rate, len(pool), seed=seed + 11)
+    out["at_4x_rate"] = {"rate_per_s": 4 * args.serve_rate,
+                         "continuous_batching": serving.run_stream(pool, hot, max_active=8, tuning=tun),
+                         "one_job_per_launch": serving.run_stream(pool, hot, max_active=1, tuning=tun)}
+    return out
 
 
 def run_reference(args):

@@ -119,7 +119,9 @@ typedef struct {
   uint32_t base_smem_set_log2;    /* (0 = the values above); it needs no queue or hot cache, so a */
                                   /* larger set fits beside a larger tile */
   uint32_t set_probes;       /* Eq. 2: positions a slot may take in the shared-memory set before it
-                                goes to the spill list (1..8; default 2, measured fastest) */
+                                goes to the spill list (1..8; default 1: fewest instructions per
+                                window, measured fastest; skipping the set for long sequences
+                                measured slower) */
   uint32_t tile_buffers;     /* corpus tiles staged by bulk copy into 2 shared-memory buffers (the
                                 next tile's copy overlaps this tile's work) when both fit, else 1;
                                 1 forces one buffer (0 = default 2) */

@@ -262,7 +262,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.queue_words = pl->queue_words;
   a.check_overflow = pl->check_overflow ? 1u : 0u;
   a.narrow = pl->narrow ? 1u : 0u;
-  a.set_probes = pl->t.set_probes ? pl->t.set_probes : 2u;
+  a.set_probes = pl->t.set_probes ? pl->t.set_probes : 1u;
   a.tile2 = pl->tile2;
   if (base) {  // the base pass's own tile and set; no queue
     a.words_per_thread = pl->base_wpt;

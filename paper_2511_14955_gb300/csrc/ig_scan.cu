@@ -581,6 +581,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     if (L < j) continue;
     const uint64_t W = L - j + 1;
     const uint32_t epoch = epoch_base + seq + 1;
+    const uint32_t sprobes = a.set_probes;
     uint32_t slog = 0, glog = 0;
     if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       uint32_t need = ceil_log2_u64(2 * W);
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
-                const int r = sset_try_insert(sset, slog, slot, a.set_probes);
+                const int r = sset_try_insert(sset, slog, slot, sprobes);
                 count_it = (r == 1);
                 if (r == 2) spill_push(spill_list, &s_nspill, slot);
               } else {
@@ -722,7 +723,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
                 if (bm) {
                   count_it = bitmap_first(bm, slot);
                 } else if (spill_list) {
-                  const int r = sset_try_insert(sset, slog, slot, a.set_probes);
+                  const int r = sset_try_insert(sset, slog, slot, sprobes);
                   count_it = (r == 1);
                   if (r == 2) spill_push(spill_list, &s_nspill, slot);
                 } else {
@@ -874,7 +875,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
-                const int r = sset_try_insert(sset, slog, slot, a.set_probes);
+                const int r = sset_try_insert(sset, slog, slot, sprobes);
                 count_it = (r == 1);
                 if (r == 2) spill_push(spill_list, &s_nspill, slot);
               } else {
@@ -989,6 +990,7 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
     const uint64_t L = a.offsets[seq + 1] - s0;
     if (L < j) continue;
     const uint64_t W = L - j + 1;
+    const uint32_t sprobes = a.set_probes;
     uint32_t slog = 0;
     if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       const uint32_t need = ceil_log2_u64(2 * W);
@@ -1083,7 +1085,7 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else {
-                const int rr = sset_try_insert(sset, slog, slot, a.set_probes);
+                const int rr = sset_try_insert(sset, slog, slot, sprobes);
                 count_it = (rr == 1);
                 if (rr == 2) spill_push(spill_list, &s_nspill, slot);
               }
