@@ -345,7 +345,8 @@ def main(argv=None):
     # end to end through the C ABI with host buffers: H2D of the corpus, every
     # pass, D2H of the top-k, inside the timed region
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(3, args.steps))
-    hplan = binding.Plan(host.numpy()[:nbytes], off, **p, graph=True, host_input=True, stream=stream)
+    hplan = binding.Plan(host.numpy()[:nbytes], off, **p, graph=True, host_input=True, stream=stream,
+                         autotune=not args.no_autotune)  # the knobs the device plan got (cached)
     hplan.run()
     hplan.topk()
     barrier()
