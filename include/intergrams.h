@@ -111,10 +111,11 @@ typedef struct {
                                 candidate: 0 = auto (when a dense map of the sigma^base_n prefixes
                                 and the counter array take at most 112 MiB together, so both stay
                                 in L2, each thread rolls the key over its own run of windows and
-                                indexes the map; otherwise the queue path of the later passes with
-                                the probe table, which measured faster there), 1 = queue path
-                                always, 2 = runs with the dense map always, 3 = runs with the hot
-                                cache and probe table (slower; kept for comparison) */
+                                indexes the map; otherwise the queue path looks the prefix up by
+                                rank/select in a bit vector of the candidate prefixes, 8 bytes per
+                                32 prefixes), 1 = queue path with the hot cache and probe table,
+                                2 = runs with the dense map, 3 = runs with the hot cache and probe
+                                table, 4 = queue path with rank/select */
   uint32_t base_words_per_thread; /* the dense base pass's own words_per_thread and smem_set_log2 */
   uint32_t base_smem_set_log2;    /* (0 = the values above); it needs no queue or hot cache, so a */
                                   /* larger set fits beside a larger tile */

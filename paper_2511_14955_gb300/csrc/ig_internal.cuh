@@ -123,6 +123,10 @@ struct ScanArgs {
   // every base-length prefix, kEmpty32 = not a candidate; null = probe table
   const uint32_t* dmap;
   uint32_t first_runs;         // pass base + 1 in per-thread window runs (no queue; no survivor lists)
+  // pass base + 1 by rank/select: word w of the candidate bit vector over the
+  // base-length prefixes with the number of candidates in words < w; the id
+  // of a candidate prefix is its position in byte order; null = not used
+  const uint2* pbits;
   uint32_t set_probes;         // bounded probe length of the shared-memory dedupe set (1..8)
   uint32_t tile2;              // word offset of the second tile buffer in dynamic smem (0 = one buffer)
   PassCtl* ctl;
@@ -174,6 +178,10 @@ void launch_build_keys(const uint32_t* sel_slot, const PassCtl* ctl, const unsig
 // probe table: key -> rank[r] (the counter row the next scan uses)
 void launch_build_table(const unsigned long long* keys, const uint32_t* rank, const PassCtl* ctl, uint4* table,
                         uint32_t table_log2, cudaStream_t s);
+// rank/select words after the base pass: bit s of word s / 32 set for every
+// selected base gram s, .y = number of selected grams in earlier words
+void launch_build_pbits(const uint32_t* sel_slot, const PassCtl* ctl, uint2* pbits, uint32_t words,
+                        uint32_t* block_sums /* ceil(words / 1024) + 1 */, cudaStream_t s);
 // dense prefix map after the base pass: dmap[sel_slot[i]] = rank[i], the rest kEmpty32
 void launch_build_dmap(const uint32_t* sel_slot, const PassCtl* ctl, const uint32_t* rank, uint32_t* dmap,
                        uint64_t entries, cudaStream_t s);

@@ -841,23 +841,33 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             wl[k] = 0xFFFFFFFFu;  // not a window
             prefix[k] = 0;
             uint64_t hp = 0;  // one multiply-shift product for the hot cache and the table
+            e[k] = make_uint4(0, 0, 0, 0);
             if (qi < q1) {
               const uint32_t w = queue[qi];
               prefix[k] = short_key ? tile_key32<SB>(tile, sym_off + w, j - 1) : tile_key<SB>(tile, sym_off + w, j - 1);
               wl[k] = (w << 8) | tile_sym<SB>(tile, sym_off + w + j - 1);
-              hp = prefix[k] * 0x9E3779B97F4A7C15ull;
-              if (H) {
-                const uint32_t h = (uint32_t)(hp >> (64 - a.hot_log2));
-                if (hot_keys[h] == prefix[k]) id[k] = hot_ids[h];
+              if (a.pbits) {  // candidate bit and the count of candidates before its word
+                const uint2 pe = __ldg(a.pbits + (prefix[k] >> 5));
+                e[k] = make_uint4(pe.x, pe.y, 0, 0);
+              } else {
+                hp = prefix[k] * 0x9E3779B97F4A7C15ull;
+                if (H) {
+                  const uint32_t h = (uint32_t)(hp >> (64 - a.hot_log2));
+                  if (hot_keys[h] == prefix[k]) id[k] = hot_ids[h];
+                }
+                if (id[k] == kEmpty32) e[k] = __ldg(a.table + (uint32_t)(hp >> (64 - a.table_log2)));
               }
             }
-            e[k] = make_uint4(0, 0, 0, 0);
-            if (wl[k] != 0xFFFFFFFFu && id[k] == kEmpty32) e[k] = __ldg(a.table + (uint32_t)(hp >> (64 - a.table_log2)));
           }
 #pragma unroll
           for (uint32_t k = 0; k < kProbeBatch; ++k) {
             if (wl[k] == 0xFFFFFFFFu) continue;
-            if (id[k] == kEmpty32) id[k] = probe_from(a.table, a.table_log2, prefix[k], e[k], a.ctl);
+            if (a.pbits) {
+              const uint32_t bit = (uint32_t)prefix[k] & 31u;
+              id[k] = ((e[k].x >> bit) & 1u) ? e[k].y + __popc(e[k].x & ((1u << bit) - 1u)) : kEmpty32;
+            } else if (id[k] == kEmpty32) {
+              id[k] = probe_from(a.table, a.table_log2, prefix[k], e[k], a.ctl);
+            }
             if (id[k] == kEmpty32) continue;
             const uint32_t qi = qb + k * nthr;
             const uint32_t w = wl[k] >> 8, last = wl[k] & 255u;

@@ -182,4 +182,63 @@ void launch_build_dmap(const uint32_t* sel_slot, const PassCtl* ctl, const uint3
   dmap_fill_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, rank, dmap);
 }
 
+namespace {
+__global__ void pbits_clear_kernel(uint2* pbits, uint32_t words) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
+    pbits[i] = make_uint2(0u, 0u);
+}
+__global__ void pbits_set_kernel(const uint32_t* sel_slot, const PassCtl* ctl, uint2* pbits) {
+  const uint32_t n = ctl->nsel;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t s = sel_slot[i];
+    atomicOr(&pbits[s >> 5].x, 1u << (s & 31));
+  }
+}
+// block b of 1024 words: exclusive prefix of popcounts within the block into
+// .y, the block's total to sums[b]
+__global__ void pbits_scan_blocks_kernel(uint2* pbits, uint32_t words, uint32_t* sums) {
+  __shared__ uint32_t sh[1024];
+  const uint32_t i = blockIdx.x * 1024 + threadIdx.x;
+  const uint32_t v = i < words ? __popc(pbits[i].x) : 0u;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (uint32_t o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
+    const uint32_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < words) pbits[i].y = sh[threadIdx.x] - v;
+  if (threadIdx.x == 1023) sums[blockIdx.x] = sh[1023];
+}
+// one block: exclusive scan of the block totals (at most 1024 blocks)
+__global__ void pbits_scan_sums_kernel(uint32_t* sums, uint32_t nblocks) {
+  __shared__ uint32_t sh[1024];
+  const uint32_t v = threadIdx.x < nblocks ? sums[threadIdx.x] : 0u;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (uint32_t o = 1; o < 1024; o <<= 1) {
+    const uint32_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (threadIdx.x < nblocks) sums[threadIdx.x] = sh[threadIdx.x] - v;
+}
+__global__ void pbits_add_kernel(uint2* pbits, uint32_t words, const uint32_t* sums) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
+    pbits[i].y += sums[i / 1024];
+}
+}  // namespace
+
+void launch_build_pbits(const uint32_t* sel_slot, const PassCtl* ctl, uint2* pbits, uint32_t words,
+                        uint32_t* block_sums, cudaStream_t s) {
+  const uint32_t nb = (words + 1023) / 1024;
+  pbits_clear_kernel<<<1024, 256, 0, s>>>(pbits, words);
+  pbits_set_kernel<<<1024, 256, 0, s>>>(sel_slot, ctl, pbits);
+  pbits_scan_blocks_kernel<<<nb, 1024, 0, s>>>(pbits, words, block_sums);
+  pbits_scan_sums_kernel<<<1, 1024, 0, s>>>(block_sums, nb);
+  pbits_add_kernel<<<1024, 256, 0, s>>>(pbits, words, block_sums);
+}
+
 }  // namespace ig

@@ -106,6 +106,7 @@ def test_dna_reduced(mode):
     dict(dense_prefix=1, words_per_thread=3),                                 # probe table in pass base + 1
     dict(dense_prefix=2, threads=512),                                        # dense map in pass base + 1
     dict(dense_prefix=3, hot_log2=7),                                         # window runs + probe table
+    dict(dense_prefix=4),                                                     # rank/select in pass base + 1
     dict(words_per_thread=3, smem_set_log2=13, base_words_per_thread=7, base_smem_set_log2=15),  # base knobs
     dict(set_probes=1, smem_set_log2=11),                                     # one-probe set, many spills
     dict(set_probes=8),
