@@ -174,45 +174,54 @@ void scheduler(ig_server* sv) {
       else running.push_back(jb);
     }
     bool progressed = !admit.empty();
-    for (Job* jb : running) {
+    // a job handed to finish_job may be deleted by its waiter at once, so it
+    // leaves the running list in the same step and is not touched again
+    for (auto it = running.begin(); it != running.end();) {
+      Job* jb = *it;
+      bool finished = false;
       if (jb->inflight) {
         const cudaError_t q = cudaEventQuery(jb->ev);
-        if (q == cudaErrorNotReady) continue;
+        if (q == cudaErrorNotReady) {
+          ++it;
+          continue;
+        }
         jb->inflight = false;
         progressed = true;
         if (q != cudaSuccess) {
           finish_job(sv, jb, IG_ECUDA, cudaGetErrorString(q));
-          continue;
-        }
-        if (jb->state == kPasses) {
+          finished = true;
+        } else if (jb->state == kPasses) {
           const ig_status st = ig::plan_last_status(jb->plan);
           if (st != IG_OK) {
             finish_job(sv, jb, st, intergrams_last_error());
-            continue;
+            finished = true;
           }
         } else if (jb->state == kTopk) {
           finish_job(sv, jb, IG_OK, "");
-          continue;
+          finished = true;
         }
       }
-      // the job's previous step is complete: enqueue its next one
-      ig_status st;
-      if (!ig::plan_passes_done(jb->plan)) {
-        jb->state = kPasses;
-        st = ig::plan_enqueue_next(jb->plan, jb->ev);
-      } else {
-        jb->state = kTopk;
-        st = ig::plan_enqueue_topk(jb->plan, jb->keys_pinned, jb->counts_pinned, jb->p.k, &jb->rows, jb->ev);
+      if (!finished) {
+        // the job's previous step is complete: enqueue its next one
+        ig_status st;
+        if (!ig::plan_passes_done(jb->plan)) {
+          jb->state = kPasses;
+          st = ig::plan_enqueue_next(jb->plan, jb->ev);
+        } else {
+          jb->state = kTopk;
+          st = ig::plan_enqueue_topk(jb->plan, jb->keys_pinned, jb->counts_pinned, jb->p.k, &jb->rows, jb->ev);
+        }
+        if (st != IG_OK) {
+          finish_job(sv, jb, st, intergrams_last_error());
+          finished = true;
+        } else {
+          jb->inflight = true;
+          progressed = true;
+        }
       }
-      if (st != IG_OK) {
-        finish_job(sv, jb, st, intergrams_last_error());
-        continue;
-      }
-      jb->inflight = true;
-      progressed = true;
+      if (finished) it = running.erase(it);
+      else ++it;
     }
-    running.erase(std::remove_if(running.begin(), running.end(), [](Job* jb) { return jb->state == kDone; }),
-                  running.end());
     if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
@@ -309,10 +318,13 @@ ig_status intergrams_server_wait(ig_server* sv, uint64_t job_id, int64_t timeout
   auto done = [&] { return jb->state == kDone; };
   if (timeout_us < 0) sv->cv_done.wait(lock, done);
   else if (!sv->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done)) return IG_ETIMEOUT;
-  const uint32_t r = std::min(capacity, jb->rows);
+  // rows of a finished job: only what finish_job copied out (nothing if it failed)
+  uint32_t r = jb->status == IG_OK ? std::min(capacity, jb->rows) : 0u;
+  r = std::min<uint64_t>(r, jb->counts.size());
+  if (jb->row_bytes) r = std::min<uint64_t>(r, jb->keys.size() / jb->row_bytes);
   if (keys_out && r) std::memcpy(keys_out, jb->keys.data(), (size_t)r * jb->row_bytes);
   if (counts_out && r) std::memcpy(counts_out, jb->counts.data(), sizeof(uint64_t) * r);
-  *k_out = jb->status == IG_OK ? r : 0;
+  *k_out = r;
   if (latency_s) *latency_s = std::chrono::duration<double>(jb->t_done - jb->t_submit).count();
   const ig_status st = jb->status;
   if (st != IG_OK) ig::set_last_error(jb->err);
