@@ -4,19 +4,28 @@
 // A persistent grid pulls whole sequences from a queue ordered longest
 // first. A CTA owns its sequence: it streams it through shared memory in
 // tiles (each tile carries a halo of j-1 symbols so windows that cross a
-// tile edge are complete), every thread rolls a j-symbol key over a
-// contiguous run of windows, and
-//   base pass      : slot = the j-gram itself (sigma^j dense counters);
-//   candidate pass : the (j-1)-gram prefix is looked up in the probe table
-//                    of P^(j-1) (ids in lexicographic order); a hit is a
-//                    survivor with slot = id * sigma + last symbol.
+// tile edge are complete; tiles arrive by bulk copy, the next one in flight
+// while the current one is processed), and
+//   base pass      : each thread rolls a j-symbol key over its run of
+//                    windows; slot = the j-gram itself (sigma^j counters);
+//   candidate pass : windows alive in the previous pass's survivor bits are
+//                    queued; a queued window's (j-1)-gram prefix is looked up
+//                    (hot cache in shared memory, then the probe table of
+//                    P^(j-1); in pass base+1 by rank/select over the
+//                    candidate bit vector of base-length prefixes, or a dense
+//                    map); a hit is a survivor with slot = row * sigma + last
+//                    symbol, and it sets its survivor bit for the next pass.
 // Under Eq. 2 a survivor is counted only the first time its slot appears in
-// the sequence: the CTA keeps the sequence's slots in a shared-memory set and
-// spills to a CTA-private global set (entries stamped with a per-(pass,
-// sequence) epoch, so they never need clearing). This is the paper's
-// per-sequence bit vector C_i, stored sparsely. Under Eq. 1 every survivor
-// counts. Counting is an atomic increment of the dense slot counter
-// (the paper's C).
+// the sequence (the paper's per-sequence bit vector C_i): a per-CTA bit
+// vector over the slots when the slot space is small, else a bounded-probe
+// shared-memory set whose overflow goes to a CTA-private spill list that is
+// hash-partitioned and deduplicated bucket by bucket at the sequence's end
+// (the allocation-free entry point uses an epoch-stamped global set
+// instead). Under Eq. 1 every survivor counts. Counting is an atomic
+// increment of the dense slot counter (the paper's C).
+//
+// chain_kernel runs a pass from the previous pass's survivor lists instead
+// of the corpus (keys longer than 64 bits).
 #include "ig_internal.cuh"
 
 namespace ig {
