@@ -126,6 +126,10 @@ typedef struct {
   uint32_t tile_buffers;     /* corpus tiles staged by bulk copy into 2 shared-memory buffers (the
                                 next tile's copy overlaps this tile's work) when both fit, else 1;
                                 1 forces one buffer (0 = default 2) */
+  uint32_t rs_depth;         /* with rank/select (dense_prefix 0 without the dense map, or 4): the
+                                first rs_depth key-probe candidate passes (1..4; default 2) look
+                                their prefix up level by level in bit vectors of the selected slots
+                                instead of the hot cache and probe table */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

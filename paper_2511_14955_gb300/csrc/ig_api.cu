@@ -133,10 +133,12 @@ struct ig_plan {
   uint64_t bitmap_bits = 0;
   // dense prefix map of the first candidate pass (sigma^b rows)
   uint32_t* dmap = nullptr;
-  // rank/select words of the first candidate pass (sigma^b / 32)
-  uint2* pbits = nullptr;
-  uint32_t* pbits_sums = nullptr;
-  uint32_t pbits_words = 0;
+  // rank/select levels: level L covers pass b + L's slots (sigma^b for L = 0,
+  // sigma * Z above) and serves candidate passes b + L + 1 .. b + rs_levels
+  uint2* rs[kMaxRsLevels] = {};
+  uint32_t rs_words[kMaxRsLevels] = {};
+  uint32_t* rs_sums = nullptr;
+  uint32_t rs_levels = 0;
   // feature matrix scratch (intergrams_features), kept until free; the count
   // stays valid until rewind
   unsigned long long* feat_keys = nullptr;
@@ -187,7 +189,7 @@ void release(ig_plan* pl) {
                   pl->list_off[1], pl->list_cnt[0], pl->list_cnt[1], pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
                   pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank,
-                  pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap, pl->dmap, pl->pbits, pl->pbits_sums, pl->feat_keys,
+                  pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap, pl->dmap, pl->rs[0], pl->rs[1], pl->rs[2], pl->rs[3], pl->rs_sums, pl->feat_keys,
                   pl->feat_table, pl->feat_q, pl->feat_nnz, pl->feat_rowptr};
   for (void* q : ptrs)
     if (q) {
@@ -221,10 +223,10 @@ bool runs_pass(const ig_plan* pl, uint32_t j) {
          mode_of(pl, j + 1) != kModeChain;
 }
 bool dense_pass(const ig_plan* pl, uint32_t j) { return pl->dmap && runs_pass(pl, j); }
-// Pass j is the first candidate pass looked up by rank/select over the
-// candidate bit vector of base-length prefixes (counters in byte-order ids).
-bool pbits_pass(const ig_plan* pl, uint32_t j) {
-  return pl->pbits && j == pl->b + 1 && mode_of(pl, j) == kModeShort && mode_of(pl, j + 1) != kModeChain;
+// Pass j looks its prefix up by rank/select through levels 0 .. j - b - 1
+// (and counts in byte-order ids).
+bool rs_pass(const ig_plan* pl, uint32_t j) {
+  return pl->rs_levels && j > pl->b && j <= pl->b + pl->rs_levels && mode_of(pl, j) == kModeShort;
 }
 
 // Kernels of one sort by count: init + (histogram, two scans, scatter) per 8-bit digit.
@@ -303,8 +305,10 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.hot = pl->hot;
   a.hot_log2 = (md == kModeShort) ? pl->hot_log2 : 0u;
   if (runs_pass(pl, j)) a.first_runs = 1;
-  if (pbits_pass(pl, j)) {
-    a.pbits = pl->pbits;
+  if (rs_pass(pl, j)) {
+    for (uint32_t L = 0; L < j - pl->b; ++L) a.rs[L] = pl->rs[L];
+    a.rs_depth = j - pl->b;
+    a.base_len = pl->b;
     a.hot_log2 = 0;
   }
   if (dense_pass(pl, j)) {
@@ -340,7 +344,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   // the scan of a candidate pass counted in rank space; selection reads the
   // counters back in byte order through the rank map
   // (a rank/select pass counts in byte-order ids: no rank map)
-  launch_select(pl->counts, pl->narrow, (base || pbits_pass(pl, j)) ? nullptr : pl->rank, pl->sb, ns, target, pl->ctl,
+  launch_select(pl->counts, pl->narrow, (base || rs_pass(pl, j)) ? nullptr : pl->rank, pl->sb, ns, target, pl->ctl,
                 pl->hist, pl->blk, pl->G, sel, pl->sel_count, s);
   kernels += 12;
   if (j < pl->p.n) {
@@ -351,7 +355,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
     if (md_next == kModeShort)
       launch_build_keys(sel, pl->ctl, pl->keys[pl->cur], base, pl->sb, pl->keys[nxt], s);
     else
-      launch_chain_keys(sel, pl->ctl, pl->rank, base, pl->sb, pl->keys[nxt], s);
+      launch_chain_keys(sel, pl->ctl, pl->rank, base || rs_pass(pl, j), pl->sb, pl->keys[nxt], s);
     launch_sort_by_count(pl->sel_count, pl->ctl, pl->sort_cap, pl->narrow ? 16u : 32u, pl->sidx[0], pl->sidx[1], pl->skey[0], pl->skey[1],
                          pl->shist, s);
     launch_rank(pl->sidx[0], pl->ctl, pl->rank, pl->p.candidates, s);
@@ -359,14 +363,14 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
     if (dense_pass(pl, j + 1)) {
       launch_build_dmap(sel, pl->ctl, pl->rank, pl->dmap, pl->nslots_base, s);
       kernels += 1;
-    } else if (pbits_pass(pl, j + 1)) {
-      launch_build_pbits(sel, pl->ctl, pl->pbits, pl->pbits_words, pl->pbits_sums, s);
+    } else if (rs_pass(pl, j + 1)) {  // level j - b from this pass's selection
+      launch_build_pbits(sel, pl->ctl, pl->rs[j - pl->b], pl->rs_words[j - pl->b], pl->rs_sums, s);
       kernels += 5;
     } else {
       launch_build_table(pl->keys[nxt], pl->rank, pl->ctl, pl->table, pl->table_log2, s);
       kernels += 2;
     }
-    if (pl->hot_log2 && md_next == kModeShort && !dense_pass(pl, j + 1) && !pbits_pass(pl, j + 1)) {
+    if (pl->hot_log2 && md_next == kModeShort && !dense_pass(pl, j + 1) && !rs_pass(pl, j + 1)) {
       launch_build_hot(pl->keys[nxt], pl->sel_count, pl->rank, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
       kernels += 3;
     }
@@ -569,7 +573,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
       t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13 || t.list_pct > 200 ||
-      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.set_probes > 8 || t.tile_buffers > 2 || t.dense_prefix > 4 || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
+      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.set_probes > 8 || t.tile_buffers > 2 || t.dense_prefix > 4 || t.rs_depth > kMaxRsLevels || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
       (t.log_range_log2 && (t.log_range_log2 < 10 || t.log_range_log2 > 30)))
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;
@@ -758,10 +762,20 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
     const bool first_ok = pl->b < p->n && mode_of(pl, pl->b + 1) == kModeShort && mode_of(pl, pl->b + 2) != kModeChain;
     if (want && first_ok) {
       PLAN_CUDA(dev_alloc(pl, &pl->dmap, pl->nslots_base));
-    } else if (first_ok && (t.dense_prefix == 0 || t.dense_prefix == 4) && pl->nslots_base <= (1ull << 24)) {
-      pl->pbits_words = (uint32_t)((pl->nslots_base + 31) / 32);
-      PLAN_CUDA(dev_alloc(pl, &pl->pbits, pl->pbits_words));
-      PLAN_CUDA(dev_alloc(pl, &pl->pbits_sums, (pl->pbits_words + 1023) / 1024 + 1));
+    } else if ((t.dense_prefix == 0 || t.dense_prefix == 4) && pl->b < p->n && pl->nslots_base <= (1ull << 24) &&
+               pl->nslots_cand <= (1ull << 35)) {
+      // rank/select for the first rs_depth candidate passes that are key-probe passes
+      const uint32_t want_levels = std::min<uint32_t>(t.rs_depth ? t.rs_depth : 2u, kMaxRsLevels);
+      uint32_t lv = 0;
+      while (lv < want_levels && pl->b + lv + 1 <= p->n && mode_of(pl, pl->b + lv + 1) == kModeShort) ++lv;
+      pl->rs_levels = lv;
+      uint32_t maxw = 1;
+      for (uint32_t L = 0; L < lv; ++L) {
+        pl->rs_words[L] = (uint32_t)(((L == 0 ? pl->nslots_base : pl->nslots_cand) + 31) / 32);
+        maxw = std::max(maxw, pl->rs_words[L]);
+        PLAN_CUDA(dev_alloc(pl, &pl->rs[L], pl->rs_words[L]));
+      }
+      if (lv) PLAN_CUDA(dev_alloc(pl, &pl->rs_sums, (maxw + 1023) / 1024 + 1));
     }
   }
   // Eq. 2 bit vectors: a pass whose slot space is small dedupes each sequence

@@ -23,6 +23,7 @@ constexpr uint32_t kMaxRuns = 64;    // runs per tile (tile windows <= 65536 / .
 // a step that registers at most chunk / 8 slots, makes room for that many in
 // each
 constexpr uint32_t kLogMaxRanges = 32;
+constexpr uint32_t kMaxRsLevels = 4;     // rank/select levels (candidate passes base + 1 .. base + 4)
 constexpr uint32_t kNoChunk = 0xFFFFFFFEu;  // range has no open chunk yet (kEmpty32: pool exhausted)
 
 // Sticky device status bits (PassCtl::status).
@@ -123,10 +124,13 @@ struct ScanArgs {
   // every base-length prefix, kEmpty32 = not a candidate; null = probe table
   const uint32_t* dmap;
   uint32_t first_runs;         // pass base + 1 in per-thread window runs (no queue; no survivor lists)
-  // pass base + 1 by rank/select: word w of the candidate bit vector over the
-  // base-length prefixes with the number of candidates in words < w; the id
-  // of a candidate prefix is its position in byte order; null = not used
-  const uint2* pbits;
+  // candidate passes base + 1 .. base + rs_depth by rank/select: level L is
+  // the bit vector over pass base + L's slots of the selected ones, each
+  // 32-bit word beside the number of selected slots in earlier words; a
+  // prefix's byte-order id follows level by level (0 = the probe table)
+  const uint2* rs[kMaxRsLevels];
+  uint32_t rs_depth;
+  uint32_t base_len;
   uint32_t set_probes;         // bounded probe length of the shared-memory dedupe set (1..8)
   uint32_t tile2;              // word offset of the second tile buffer in dynamic smem (0 = one buffer)
   PassCtl* ctl;

@@ -408,6 +408,7 @@ __device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* warp_to
 // latency with one CTA per SM.
 constexpr uint32_t kBatch = 8;
 constexpr uint32_t kProbeBatch = 4;
+constexpr uint32_t kDead = 0xFFFFFFFDu;  // rank/select chain: a level's bit was clear
 
 // Exact dedupe of src[lo, hi) in a cleared table at the front of the
 // shared-memory set, sized to at least twice the entries (at most the whole
@@ -853,12 +854,13 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             e[k] = make_uint4(0, 0, 0, 0);
             if (qi < q1) {
               const uint32_t w = queue[qi];
-              prefix[k] = short_key ? tile_key32<SB>(tile, sym_off + w, j - 1) : tile_key<SB>(tile, sym_off + w, j - 1);
               wl[k] = (w << 8) | tile_sym<SB>(tile, sym_off + w + j - 1);
-              if (a.pbits) {  // candidate bit and the count of candidates before its word
-                const uint2 pe = __ldg(a.pbits + (prefix[k] >> 5));
+              if (a.rs_depth) {  // level 0: the base-length prefix; its word and the count before it
+                prefix[k] = tile_key32<SB>(tile, sym_off + w, a.base_len);
+                const uint2 pe = __ldg(a.rs[0] + (prefix[k] >> 5));
                 e[k] = make_uint4(pe.x, pe.y, 0, 0);
               } else {
+                prefix[k] = short_key ? tile_key32<SB>(tile, sym_off + w, j - 1) : tile_key<SB>(tile, sym_off + w, j - 1);
                 hp = prefix[k] * 0x9E3779B97F4A7C15ull;
                 if (H) {
                   const uint32_t h = (uint32_t)(hp >> (64 - a.hot_log2));
@@ -868,15 +870,36 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               }
             }
           }
+          if (a.rs_depth) {
+            // rank/select chain: the byte-order id of the prefix's first
+            // base_len + L symbols at level L is its position among the
+            // selected slots of pass base + L (all levels' loads of a round
+            // are issued together)
+            for (uint32_t L = 0;; ++L) {
+#pragma unroll
+              for (uint32_t k = 0; k < kProbeBatch; ++k) {
+                if (wl[k] == 0xFFFFFFFFu || id[k] == kDead) continue;
+                const uint32_t bit = (uint32_t)prefix[k] & 31u;
+                id[k] = ((e[k].x >> bit) & 1u) ? e[k].y + __popc(e[k].x & ((1u << bit) - 1u)) : kDead;
+              }
+              if (L + 1 >= a.rs_depth) break;
+#pragma unroll
+              for (uint32_t k = 0; k < kProbeBatch; ++k) {
+                if (wl[k] == 0xFFFFFFFFu || id[k] == kDead) continue;
+                const uint32_t w = wl[k] >> 8;
+                prefix[k] = ((uint64_t)id[k] << SB) | tile_sym<SB>(tile, sym_off + w + a.base_len + L);
+                const uint2 pe = __ldg(a.rs[L + 1] + (prefix[k] >> 5));
+                e[k] = make_uint4(pe.x, pe.y, 0, 0);
+              }
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < kProbeBatch; ++k)
+              if (id[k] == kDead) id[k] = kEmpty32;
+          }
 #pragma unroll
           for (uint32_t k = 0; k < kProbeBatch; ++k) {
             if (wl[k] == 0xFFFFFFFFu) continue;
-            if (a.pbits) {
-              const uint32_t bit = (uint32_t)prefix[k] & 31u;
-              id[k] = ((e[k].x >> bit) & 1u) ? e[k].y + __popc(e[k].x & ((1u << bit) - 1u)) : kEmpty32;
-            } else if (id[k] == kEmpty32) {
-              id[k] = probe_from(a.table, a.table_log2, prefix[k], e[k], a.ctl);
-            }
+            if (!a.rs_depth && id[k] == kEmpty32) id[k] = probe_from(a.table, a.table_log2, prefix[k], e[k], a.ctl);
             if (id[k] == kEmpty32) continue;
             const uint32_t qi = qb + k * nthr;
             const uint32_t w = wl[k] >> 8, last = wl[k] & 255u;

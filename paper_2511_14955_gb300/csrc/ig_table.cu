@@ -211,19 +211,28 @@ __global__ void pbits_scan_blocks_kernel(uint2* pbits, uint32_t words, uint32_t*
   if (i < words) pbits[i].y = sh[threadIdx.x] - v;
   if (threadIdx.x == 1023) sums[blockIdx.x] = sh[1023];
 }
-// one block: exclusive scan of the block totals (at most 1024 blocks)
+// one block: exclusive scan of the block totals, 1024 at a time with a carry
 __global__ void pbits_scan_sums_kernel(uint32_t* sums, uint32_t nblocks) {
   __shared__ uint32_t sh[1024];
-  const uint32_t v = threadIdx.x < nblocks ? sums[threadIdx.x] : 0u;
-  sh[threadIdx.x] = v;
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (uint32_t o = 1; o < 1024; o <<= 1) {
-    const uint32_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0u;
+  for (uint32_t c0 = 0; c0 < nblocks; c0 += 1024) {
+    const uint32_t i = c0 + threadIdx.x;
+    const uint32_t v = i < nblocks ? sums[i] : 0u;
+    sh[threadIdx.x] = v;
     __syncthreads();
-    sh[threadIdx.x] += t;
+    for (uint32_t o = 1; o < 1024; o <<= 1) {
+      const uint32_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0u;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nblocks) sums[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
     __syncthreads();
   }
-  if (threadIdx.x < nblocks) sums[threadIdx.x] = sh[threadIdx.x] - v;
 }
 __global__ void pbits_add_kernel(uint2* pbits, uint32_t words, const uint32_t* sums) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)

@@ -106,7 +106,9 @@ def test_dna_reduced(mode):
     dict(dense_prefix=1, words_per_thread=3),                                 # probe table in pass base + 1
     dict(dense_prefix=2, threads=512),                                        # dense map in pass base + 1
     dict(dense_prefix=3, hot_log2=7),                                         # window runs + probe table
-    dict(dense_prefix=4),                                                     # rank/select in pass base + 1
+    dict(dense_prefix=4),                                                     # rank/select in passes base + 1, + 2
+    dict(dense_prefix=4, rs_depth=4, words_per_thread=3),                     # four rank/select levels
+    dict(dense_prefix=4, rs_depth=1, hot_log2=8),
     dict(words_per_thread=3, smem_set_log2=13, base_words_per_thread=7, base_smem_set_log2=15),  # base knobs
     dict(set_probes=1, smem_set_log2=11),                                     # one-probe set, many spills
     dict(set_probes=8),
@@ -158,6 +160,14 @@ def test_chain_mode_with_short_keys(mode):
     """Chain passes from pass base+2 on (short keys), against every pass of the oracle."""
     data, off, _ = synth.make_corpus("malware_8gb", m=30, max_len=40000, seed=8)
     check_all_passes(data, off, n=8, k=300, Z=1200, base_n=2, mode=mode, tuning=dict(chain_from=4))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chain_passes_after_rank_select_passes(mode):
+    """Rank/select passes (counting in byte-order ids) followed by passes run from survivor lists."""
+    data, off, _ = synth.make_corpus("malware_8gb", m=30, max_len=40000, seed=12)
+    check_all_passes(data, off, n=8, k=300, Z=1200, base_n=2, mode=mode,
+                     tuning=dict(chain_from=5, dense_prefix=4, rs_depth=3))
 
 
 def test_list_capacity_exceeded_is_reported():
