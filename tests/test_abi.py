@@ -35,3 +35,24 @@ def test_null_arguments_rejected_without_gpu():
     assert lib.intergrams_pass(None, None) == -1
     assert lib.intergrams_run(None) == -1
     lib.intergrams_free(None)
+
+
+def struct_fields(name):
+    """uint32_t fields of `typedef struct { ... } name;` in the header, in order."""
+    text = (ROOT / "include" / "intergrams.h").read_text()
+    end = text.index("} " + name + ";")
+    body = text[text.rindex("typedef struct {", 0, end):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return re.findall(r"uint32_t\s+(\w+)\s*;", body)
+
+
+def test_tuning_struct_matches_header():
+    """The binding's IgTuning lists the header's ig_tuning fields in order (all uint32_t)."""
+    fields = struct_fields("ig_tuning")
+    assert [f for f, _ in binding.IgTuning._fields_] == fields
+    assert ctypes.sizeof(binding.IgTuning) == 4 * len(fields)
+
+
+def test_params_struct_matches_header():
+    fields = struct_fields("ig_params")
+    assert [f for f, _ in binding.IgParams._fields_] == fields
