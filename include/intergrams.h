@@ -345,6 +345,32 @@ void intergrams_free(ig_plan* pl);
 /* Message describing the last error on the calling thread ("" if none). */
 const char* intergrams_last_error(void);
 
+/*
+ * Test hooks: failures made on the host, for testing the error paths (no
+ * counterpart in the paper; nothing here faults, traps or hangs a device).
+ *
+ * intergrams_test_fail_alloc - the nth device allocation the library makes
+ * from now on (any plan, any thread) fails as if the device were out of
+ * memory, so the call making it returns IG_ENOMEM; nth = 0 disarms.
+ *   live_out : optional; receives the number of device allocations the
+ *              library currently holds (all plans), so a test can check that
+ *              a failed call released everything it had allocated.
+ * Always returns IG_OK.
+ */
+ig_status intergrams_test_fail_alloc(uint32_t nth, uint64_t* live_out);
+
+/*
+ * intergrams_test_stall_tiles - every later corpus scan of `pl` waits for
+ * shared-memory tiles whose copies are never issued: each scan CTA's bounded
+ * wait (about one second) runs out, the CTA stops, and the pass returns
+ * IG_ETIMEOUT (the scan's results are then incomplete; free the plan). The
+ * device and other plans stay usable. Chain passes stage no tiles and are
+ * unaffected.
+ * Errors: IG_EINVAL (NULL plan), IG_ESTATE (plan made with IG_F_GRAPH, whose
+ * captured launches the hook cannot reach).
+ */
+ig_status intergrams_test_stall_tiles(ig_plan* pl);
+
 #ifdef __cplusplus
 }
 #endif

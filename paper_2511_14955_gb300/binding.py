@@ -29,7 +29,8 @@ EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_r
            "intergrams_stats", "intergrams_timings", "intergrams_free", "intergrams_last_error",
            "intergrams_dense_topk_static", "intergrams_plan_device_bytes", "intergrams_server_create",
            "intergrams_server_submit", "intergrams_server_wait", "intergrams_server_stats",
-           "intergrams_server_destroy", "intergrams_autotune", "intergrams_features"]
+           "intergrams_server_destroy", "intergrams_autotune", "intergrams_features",
+           "intergrams_test_fail_alloc", "intergrams_test_stall_tiles"]
 
 
 class IgParams(ctypes.Structure):
@@ -126,6 +127,10 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(IgTuning), ctypes.POINTER(ctypes.c_float)]
     lib.intergrams_last_error.restype = ctypes.c_char_p
     lib.intergrams_last_error.argtypes = []
+    lib.intergrams_test_fail_alloc.restype = ctypes.c_int
+    lib.intergrams_test_fail_alloc.argtypes = [U32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.intergrams_test_stall_tiles.restype = ctypes.c_int
+    lib.intergrams_test_stall_tiles.argtypes = [P]
     _lib = lib
     return lib
 
@@ -243,6 +248,11 @@ class Plan:
         r = npass.value
         return scan[:r].copy(), pas[:r].copy(), kern.value
 
+    def test_stall_tiles(self):
+        """Test hook: later corpus scans wait for tiles that are never sent,
+        so their passes raise IG_ETIMEOUT after about a second."""
+        _check(self._lib, self._lib.intergrams_test_stall_tiles(self._h), "intergrams_test_stall_tiles")
+
     def close(self):
         if self._h and self._h.value:
             self._lib.intergrams_free(self._h)
@@ -259,6 +269,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def test_fail_alloc(nth: int) -> int:
+    """Test hook: the nth device allocation of the library from now on fails
+    as out of memory (0 disarms). Returns the device allocations held now."""
+    lib = load()
+    live = ctypes.c_uint64(0)
+    lib.intergrams_test_fail_alloc(int(nth), ctypes.byref(live))
+    return live.value
 
 
 def dense_topk_static(data, offsets, *, n: int, k: int, symbol_bits: int = 8,

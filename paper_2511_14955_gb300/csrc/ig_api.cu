@@ -7,6 +7,7 @@
 // of a pass is fixed; with IG_F_GRAPH the whole remaining pass sequence is
 // captured once as a CUDA graph and replayed by later runs of the same plan.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <numeric>
@@ -41,6 +42,34 @@ namespace ig {
 // Lets other translation units record a message for intergrams_last_error().
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace ig
+
+namespace {
+
+// Every device allocation of the library goes through these two, so a test
+// can make the n-th allocation fail (host-side fault injection) and check
+// that nothing stays allocated after a failed call.
+std::atomic<uint32_t> g_fail_alloc_in{0};  // the allocation this many from now fails (0 = none)
+std::atomic<int64_t> g_live_allocs{0};
+
+cudaError_t device_malloc(void** p, size_t bytes, bool async, cudaStream_t s) {
+  *p = nullptr;
+  uint32_t n = g_fail_alloc_in.load();
+  while (n && !g_fail_alloc_in.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) return cudaErrorMemoryAllocation;
+  const cudaError_t e = async ? cudaMallocAsync(p, bytes, s) : cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+void device_free(void* q, bool async, cudaStream_t s) {
+  if (!q) return;
+  if (async) cudaFreeAsync(q, s);
+  else cudaFree(q);
+  g_live_allocs.fetch_sub(1);
+}
+
+}  // namespace
 
 struct ig_plan {
   ig_params p{};
@@ -119,6 +148,7 @@ struct ig_plan {
   uint32_t graph_kernels = 0;        // kernels in the captured graph
   uint64_t dev_bytes = 0;            // device bytes allocated (or that would be, with IG_F_DRY_RUN)
   bool dry_run = false, async_alloc = false;
+  uint32_t test_stall_tiles = 0;  // test hook: scans wait for tiles that are never sent
   cudaGraphExec_t graph = nullptr;  // full job from the first pass (IG_F_GRAPH)
   cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
   bool check_overflow = false;
@@ -162,8 +192,7 @@ cudaError_t dev_alloc(ig_plan* pl, T** p, size_t count) {
   const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
   pl->dev_bytes += bytes;
   if (pl->dry_run) return cudaSuccess;
-  if (pl->async_alloc) return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, pl->stream);
-  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  return device_malloc(reinterpret_cast<void**>(p), bytes, pl->async_alloc, pl->stream);
 }
 
 uint32_t row_bytes_for(const ig_plan* pl, uint32_t j) { return (j * pl->sb + 7) / 8; }
@@ -191,11 +220,7 @@ void release(ig_plan* pl) {
                   pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank,
                   pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap, pl->dmap, pl->rs[0], pl->rs[1], pl->rs[2], pl->rs[3], pl->rs_sums, pl->feat_keys,
                   pl->feat_table, pl->feat_q, pl->feat_nnz, pl->feat_rowptr};
-  for (void* q : ptrs)
-    if (q) {
-      if (pl->async_alloc) cudaFreeAsync(q, pl->stream);
-      else cudaFree(q);
-    }
+  for (void* q : ptrs) device_free(q, pl->async_alloc, pl->stream);
   if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
   delete pl;
 }
@@ -275,6 +300,7 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.narrow = pl->narrow ? 1u : 0u;
   a.set_probes = pl->t.set_probes ? pl->t.set_probes : 1u;
   a.tile2 = pl->tile2;
+  a.stall_tiles = pl->test_stall_tiles;
   if (base) {  // the base pass's own tile and set; no queue
     a.words_per_thread = pl->base_wpt;
     a.sset_log2 = pl->base_sset_log2;
@@ -952,11 +978,15 @@ ig_status intergrams_features(ig_plan* pl, uint64_t* row_ptr, uint32_t* cols, ui
       uint32_t tl = 8;
       while ((1u << tl) < 4ull * std::max(pl->p.k, 1u)) ++tl;
       pl->feat_table_log2 = tl;
-      IG_CUDA(cudaMalloc(&pl->feat_keys, sizeof(unsigned long long) * std::max(pl->p.k, 1u)));
-      IG_CUDA(cudaMalloc(&pl->feat_table, sizeof(uint4) << tl));
-      IG_CUDA(cudaMalloc(&pl->feat_q, 4 * sizeof(uint32_t)));
-      IG_CUDA(cudaMalloc(&pl->feat_nnz, sizeof(uint32_t) * std::max<uint32_t>(pl->m, 1)));
-      IG_CUDA(cudaMalloc(&pl->feat_rowptr, sizeof(uint64_t) * ((size_t)pl->m + 1)));
+      // each buffer once: a failed call keeps what it got for the next one
+      auto get = [&](auto** q, size_t bytes) {
+        return *q ? cudaSuccess : device_malloc(reinterpret_cast<void**>(q), bytes, false, s);
+      };
+      IG_CUDA(get(&pl->feat_keys, sizeof(unsigned long long) * std::max(pl->p.k, 1u)));
+      IG_CUDA(get(&pl->feat_table, sizeof(uint4) << tl));
+      IG_CUDA(get(&pl->feat_nnz, sizeof(uint32_t) * std::max<uint32_t>(pl->m, 1)));
+      IG_CUDA(get(&pl->feat_rowptr, sizeof(uint64_t) * ((size_t)pl->m + 1)));
+      IG_CUDA(get(&pl->feat_q, 4 * sizeof(uint32_t)));
     }
     IG_CUDA(feature_set_smem(pl->sb, fsmem));
     IG_CUDA(cudaMemsetAsync(pl->feat_q, 0, 4 * sizeof(uint32_t), s));
@@ -976,7 +1006,7 @@ ig_status intergrams_features(ig_plan* pl, uint64_t* row_ptr, uint32_t* cols, ui
   if (cols && capacity < pl->feat_total) return fail(IG_EINVAL, "cols capacity is below the number of nonzeros");
   if (cols && pl->feat_total) {
     uint32_t* d_cols = nullptr;
-    IG_CUDA(cudaMalloc(&d_cols, sizeof(uint32_t) * pl->feat_total));
+    IG_CUDA(device_malloc(reinterpret_cast<void**>(&d_cols), sizeof(uint32_t) * pl->feat_total, false, s));
     cudaError_t e = cudaMemsetAsync(pl->feat_q + 1, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) {
       launch_features(pl->data, pl->data_bytes, pl->offsets, pl->d_order, pl->m, pl->p.n, pl->sb, pl->out_keys,
@@ -986,7 +1016,7 @@ ig_status intergrams_features(ig_plan* pl, uint64_t* row_ptr, uint32_t* cols, ui
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
-    cudaFree(d_cols);
+    device_free(d_cols, false, s);
     if (e != cudaSuccess) return fail(IG_ECUDA, cudaGetErrorString(e));
   }
   if (row_ptr) {
@@ -1032,6 +1062,20 @@ ig_status intergrams_timings(ig_plan* pl, float* scan_ms, float* pass_ms, uint32
     if (pass_ms) IG_CUDA(cudaEventElapsedTime(pass_ms + i, pl->ev_pass0[i], pl->ev_pass1[i]));
   }
   *npasses = np;
+  return IG_OK;
+}
+
+ig_status intergrams_test_fail_alloc(uint32_t nth, uint64_t* live_out) {
+  g_fail_alloc_in.store(nth);
+  if (live_out) *live_out = (uint64_t)std::max<int64_t>(0, g_live_allocs.load());
+  return IG_OK;
+}
+
+ig_status intergrams_test_stall_tiles(ig_plan* pl) {
+  g_last_error.clear();
+  if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  if (pl->p.flags & IG_F_GRAPH) return fail(IG_ESTATE, "the stall hook needs pass-by-pass launches (no IG_F_GRAPH)");
+  pl->test_stall_tiles = 1;
   return IG_OK;
 }
 

@@ -174,10 +174,19 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait for phase `parity` of `bar`; false if it did not complete.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for phase `parity` of `bar`: false if it did not complete
+// within kTileWaitNs of global time (or 2^31 polls, whichever comes first).
+constexpr uint64_t kTileWaitNs = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t addr = smem_addr(bar);
-  for (uint32_t it = 0; it < (1u << 24); ++it) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0; it < (1u << 31); ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -185,6 +194,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 31u) == 0) {
+      const uint64_t t = global_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > kTileWaitNs) return false;
+    }
   }
   return false;
 }
@@ -197,7 +211,7 @@ __device__ __forceinline__ void stage_issue(const ScanArgs& a, const TileGeom& g
   const uintptr_t ia = g.al > lo16 ? g.al : lo16;
   const uintptr_t ie = (g.al + g.nbytes) < hi16 ? (g.al + g.nbytes) : hi16;
   const uint32_t bytes = ie > ia ? (uint32_t)(ie - ia) : 0u;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !a.stall_tiles) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
@@ -578,6 +592,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
 
   unsigned long long my_surv = 0, my_regs = 0;
   if (tid == 0) { s_surv = 0; s_regs = 0; }
+  bool stopped = false;  // a tile wait ran out
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(&a.ctl->queue, 1u);
@@ -618,9 +633,20 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
       const uint64_t gsym = g.gsym;
       const uint32_t bsel = a.tile2 ? (tix & 1u) : 0u;
       uint32_t* tile = bsel ? tile1 : tile0;
-      if (!mbar_wait(s_bar + bsel, (bar_phases >> bsel) & 1u)) atomicOr(&a.ctl->status, kStTimeout);
+      const uint32_t parity = (bar_phases >> bsel) & 1u;
+      const bool arrived = mbar_wait(s_bar + bsel, parity);
       bar_phases ^= 1u << bsel;
-      __syncthreads();  // edge chunks written by other threads are visible
+      // (the barrier also makes edge chunks written by other threads visible)
+      if (__syncthreads_or(!arrived)) {
+        // the tile did not arrive in time: report it, let a copy still in
+        // flight land (bounded again) and stop this CTA
+        if (tid == 0) {
+          atomicOr(&a.ctl->status, kStTimeout);
+          if (!a.stall_tiles) mbar_wait(s_bar + bsel, parity);
+        }
+        stopped = true;
+        break;
+      }
       if (a.tile2 && w0 + tile_windows < W)
         stage_issue(a, tile_geom<SB>(a, s0, W, w0 + tile_windows, tile_windows, j),
                     reinterpret_cast<uint8_t*>(bsel ? tile0 : tile1), s_bar + (bsel ^ 1u));
@@ -959,6 +985,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
         stage_issue(a, tile_geom<SB>(a, s0, W, w0 + tile_windows, tile_windows, j),
                     reinterpret_cast<uint8_t*>(tile0), &s_bar[0]);
     }
+    if (stopped) break;  // uniform: every thread saw the same barrier result
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       const uint32_t nsp = s_nspill;  // read after the tile loop's final barrier
       if (nsp) dedupe_spills(a, lg, nsp, sset, tile0, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
