@@ -130,6 +130,9 @@ typedef struct {
                                 first rs_depth key-probe candidate passes (1..4; default 2) look
                                 their prefix up level by level in bit vectors of the selected slots
                                 instead of the hot cache and probe table */
+  uint32_t tile_cache_hint;  /* L2 policy of the corpus tile copies: 1 = none, 2 = evict first (read
+                                once per pass, so the counters, spill lists and tables keep L2);
+                                0 = default (2) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

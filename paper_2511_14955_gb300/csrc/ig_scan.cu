@@ -215,12 +215,23 @@ __device__ __forceinline__ void stage_issue(const ScanArgs& a, const TileGeom& g
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
-    if (bytes)
+    if (bytes && a.tile_evict_first) {
+      // the corpus is read once per pass: its lines go first, so the
+      // counters, spill lists and tables stay in L2
+      uint64_t pol;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+          "%4;" ::"r"(smem_addr(buf + (ia - g.al))),
+          "l"(ia), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+          : "memory");
+    } else if (bytes) {
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
               smem_addr(buf + (ia - g.al))),
           "l"(ia), "r"(bytes), "r"(smem_addr(bar))
           : "memory");
+    }
   }
   for (uint32_t x = threadIdx.x * 16u; x < g.nbytes; x += blockDim.x * 16u) {
     const uintptr_t p = g.al + x;

@@ -112,6 +112,7 @@ def test_dna_reduced(mode):
     dict(words_per_thread=3, smem_set_log2=13, base_words_per_thread=7, base_smem_set_log2=15),  # base knobs
     dict(set_probes=1, smem_set_log2=11),                                     # one-probe set, many spills
     dict(set_probes=8),
+    dict(tile_cache_hint=1, tile_buffers=1),                                  # plain tile copies, one buffer
 ])
 def test_results_do_not_depend_on_tuning(tuning):
     data, off, _ = synth.make_corpus("markov_2mb", seed=2)
