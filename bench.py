@@ -380,8 +380,9 @@ def main(argv=None):
     del plan
 
     # end to end through the C ABI with host buffers: H2D of the corpus, every
-    # pass, D2H of the top-k, inside the timed region
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(3, args.steps))
+    # pass, D2H of the top-k, inside the timed region; each step's corpus copy
+    # is started (intergrams_prefetch) while the step before it runs
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(5, args.steps))
     hplan = binding.Plan(host.numpy()[:nbytes], off, **p, graph=True, host_input=True, stream=stream,
                          autotune=not args.no_autotune)  # the knobs the device plan got (cached)
     hplan.run()
@@ -390,8 +391,10 @@ def main(argv=None):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     d2h = 0
-    for _ in range(e2e_steps):
-        hplan.rewind()
+    for i in range(e2e_steps):
+        hplan.rewind()          # step 0 copies here; later steps take the prefetched copy
+        if i + 1 < e2e_steps:
+            hplan.prefetch()    # the next step's copy overlaps this step's passes
         hplan.run()
         keys, counts, _ = hplan.topk()
         d2h = keys.nbytes + counts.nbytes
@@ -427,7 +430,10 @@ def main(argv=None):
                    "launch": "one persistent scan per pass, CUDA graph per job",
                    "l2": "inputs larger than L2 (corpus 8.4 GB vs 129 MB L2)",
                    "parallelism": f"independent jobs x{world}"},
-        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps,
+                "pipelining": "each step's corpus copy runs while the step before it computes "
+                              "(intergrams_prefetch); the first step's copy is not overlapped"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

@@ -196,6 +196,23 @@ ig_status intergrams_run(ig_plan* pl);
 ig_status intergrams_rewind(ig_plan* pl);
 
 /*
+ * intergrams_prefetch - with IG_F_HOST_INPUT: start copying the next run's
+ * corpus (same offsets and size) from `host_data` (NULL = the buffer given to
+ * intergrams_plan) into a second device buffer of the plan, on a copy stream
+ * of its own, so the copy overlaps the passes still queued on the current
+ * buffer (no counterpart in the paper: input pipelining for repeated jobs).
+ * The next intergrams_rewind switches to that buffer, and the work queued
+ * after it waits for the copy, instead of copying again. The copy first
+ * waits for the work that read the buffer it overwrites. host_data must stay
+ * valid and unchanged until that next run has finished. The second buffer
+ * (the corpus size) is allocated at the first call and kept until
+ * intergrams_free; with IG_F_GRAPH each buffer gets its own captured graph.
+ * Errors: IG_EINVAL (NULL plan), IG_ESTATE (plan without IG_F_HOST_INPUT, or
+ * a prefetch already pending), IG_ENOMEM, IG_ECUDA.
+ */
+ig_status intergrams_prefetch(ig_plan* pl, const void* host_data);
+
+/*
  * intergrams_topk - the top-k j-grams of the latest completed pass j (paper
  * Algorithm 3, final k-argmax; after pass j < n this is the top-k of that
  * intermediate pass).

@@ -30,7 +30,7 @@ EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_r
            "intergrams_dense_topk_static", "intergrams_plan_device_bytes", "intergrams_server_create",
            "intergrams_server_submit", "intergrams_server_wait", "intergrams_server_stats",
            "intergrams_server_destroy", "intergrams_autotune", "intergrams_features",
-           "intergrams_test_fail_alloc", "intergrams_test_stall_tiles"]
+           "intergrams_test_fail_alloc", "intergrams_test_stall_tiles", "intergrams_prefetch"]
 
 
 class IgParams(ctypes.Structure):
@@ -129,6 +129,8 @@ def load(build_if_missing: bool = True):
     lib.intergrams_last_error.argtypes = []
     lib.intergrams_test_fail_alloc.restype = ctypes.c_int
     lib.intergrams_test_fail_alloc.argtypes = [U32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.intergrams_prefetch.restype = ctypes.c_int
+    lib.intergrams_prefetch.argtypes = [P, P]
     lib.intergrams_test_stall_tiles.restype = ctypes.c_int
     lib.intergrams_test_stall_tiles.argtypes = [P]
     _lib = lib
@@ -203,6 +205,20 @@ class Plan:
 
     def rewind(self):
         _check(self._lib, self._lib.intergrams_rewind(self._h), "intergrams_rewind")
+
+    def prefetch(self, data=None):
+        """With host input: start copying the next run's corpus (``data``, a
+        numpy array of the same size, or the plan's own host buffer) into the
+        plan's second device buffer; the next rewind switches to it."""
+        if data is not None:
+            data = np.ascontiguousarray(data, dtype=np.uint8)
+            if data.nbytes != self._keep[0].nbytes:
+                raise ValueError("prefetch needs a corpus of the plan's size")
+            # kept alive until its copy has certainly landed: the copy queued
+            # after it on the same copy stream starts only once it has
+            self._next = (getattr(self, "_next", (None, None))[1], data)
+        _check(self._lib, self._lib.intergrams_prefetch(self._h, None if data is None else data.ctypes.data),
+               "intergrams_prefetch")
 
     def topk(self, capacity: int | None = None):
         """(keys, counts, j): keys is a (rows, ceil(j*bits/8)) uint8 array."""

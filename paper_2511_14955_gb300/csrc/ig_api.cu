@@ -142,6 +142,15 @@ struct ig_plan {
   uint32_t out_cap = 0;
 
   const void* host_data = nullptr;   // IG_F_HOST_INPUT: re-read by intergrams_rewind
+  // intergrams_prefetch: a second device copy of the corpus, filled on a copy
+  // stream while the passes on the current one run; rewind switches to it
+  uint8_t* own_data_alt = nullptr;
+  uint32_t data_slot = 0;            // 0: own_data is current, 1: own_data_alt
+  bool prefetched = false;           // a copy into the other slot is pending
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied = nullptr;   // the pending copy has landed
+  cudaEvent_t ev_left[2] = {nullptr, nullptr};  // the work reading slot s was all queued before this
+  cudaGraphExec_t graph_alt = nullptr;  // the job's graph over own_data_alt
   // IG_F_TIMING: events around each pass and its scan, indexed by j - b
   std::vector<cudaEvent_t> ev_pass0, ev_pass1, ev_scan0, ev_scan1;
   uint32_t kernels = 0;              // kernels launched since the last rewind
@@ -209,11 +218,15 @@ uint64_t windows_for(const ig_plan* pl, uint32_t j) {
 void release(ig_plan* pl) {
   if (!pl) return;
   if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  if (pl->graph_alt) cudaGraphExecDestroy(pl->graph_alt);
+  for (cudaEvent_t e : {pl->ev_copied, pl->ev_left[0], pl->ev_left[1]})
+    if (e) cudaEventDestroy(e);
+  if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
   for (auto* v : {&pl->ev_pass0, &pl->ev_pass1, &pl->ev_scan0, &pl->ev_scan1})
     for (cudaEvent_t e : *v)
       if (e) cudaEventDestroy(e);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
-  void* ptrs[] = {pl->own_data, pl->own_offsets, pl->counts, pl->table, pl->keys[0], pl->keys[1],
+  void* ptrs[] = {pl->own_data, pl->own_data_alt, pl->own_offsets, pl->counts, pl->table, pl->keys[0], pl->keys[1],
                   pl->sel_hist, pl->sel_count, pl->d_tile_base, pl->lists[0], pl->lists[1], pl->list_off[0],
                   pl->list_off[1], pl->list_cnt[0], pl->list_cnt[1], pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
@@ -875,7 +888,9 @@ ig_status intergrams_run(ig_plan* pl) {
   if (pl->next_j > pl->p.n) return IG_OK;
   const bool from_start = pl->next_j == pl->b;
   if ((pl->p.flags & IG_F_GRAPH) && from_start) {
-    if (!pl->graph) {
+    // one graph per corpus buffer (the scans' arguments name the buffer)
+    cudaGraphExec_t& graph = pl->data_slot ? pl->graph_alt : pl->graph;
+    if (!graph) {
       // capture on a private stream (the legacy default stream cannot be
       // captured); the graph is then launched on the plan's stream
       cudaGraph_t g = nullptr;
@@ -890,11 +905,11 @@ ig_status intergrams_run(ig_plan* pl) {
       pl->cur = cur0;
       cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
       if (e != cudaSuccess) return fail(IG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&pl->graph, g, 0);
+      e = cudaGraphInstantiate(&graph, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return fail(IG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
-    IG_CUDA(cudaGraphLaunch(pl->graph, pl->stream));
+    IG_CUDA(cudaGraphLaunch(graph, pl->stream));
     pl->kernels += pl->graph_kernels;
     for (uint32_t j = pl->b; j <= pl->p.n; ++j) finish_pass_host(pl, j);
     return read_status(pl);
@@ -916,8 +931,43 @@ ig_status intergrams_rewind(ig_plan* pl) {
   pl->nsel_last = 0;
   pl->kernels = 0;
   pl->feat_ready = false;
+  if (pl->prefetched) {
+    // switch to the prefetched buffer: everything queued so far read the old
+    // one; what follows waits for the copy
+    IG_CUDA(cudaEventRecord(pl->ev_left[pl->data_slot], pl->stream));
+    pl->data_slot ^= 1u;
+    pl->data = pl->data_slot ? pl->own_data_alt : pl->own_data;
+    IG_CUDA(cudaStreamWaitEvent(pl->stream, pl->ev_copied, 0));
+    pl->prefetched = false;
+    return IG_OK;
+  }
   if ((pl->p.flags & IG_F_HOST_INPUT) && pl->data_bytes)
-    IG_CUDA(cudaMemcpyAsync(pl->own_data, pl->host_data, pl->data_bytes, cudaMemcpyHostToDevice, pl->stream));
+    IG_CUDA(cudaMemcpyAsync(const_cast<uint8_t*>(pl->data), pl->host_data, pl->data_bytes, cudaMemcpyHostToDevice,
+                            pl->stream));
+  return IG_OK;
+}
+
+ig_status intergrams_prefetch(ig_plan* pl, const void* host_data) {
+  g_last_error.clear();
+  if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  if (!(pl->p.flags & IG_F_HOST_INPUT) || pl->dry_run) return fail(IG_ESTATE, "prefetch needs a plan made with IG_F_HOST_INPUT");
+  if (pl->prefetched) return fail(IG_ESTATE, "a prefetch is already pending (rewind first)");
+  if (!host_data) host_data = pl->host_data;
+  if (!pl->data_bytes) {  // nothing to copy; the switch is a no-op
+    pl->prefetched = false;
+    return IG_OK;
+  }
+  if (!pl->copy_stream) IG_CUDA(cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&pl->ev_copied, &pl->ev_left[0], &pl->ev_left[1]})
+    if (!*e) IG_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  if (!pl->own_data_alt) IG_CUDA(dev_alloc(pl, &pl->own_data_alt, pl->data_bytes));
+  const uint32_t other = pl->data_slot ^ 1u;
+  uint8_t* dst = other ? pl->own_data_alt : pl->own_data;
+  // the other buffer may still be read by work queued before it was left
+  IG_CUDA(cudaStreamWaitEvent(pl->copy_stream, pl->ev_left[other], 0));
+  IG_CUDA(cudaMemcpyAsync(dst, host_data, pl->data_bytes, cudaMemcpyHostToDevice, pl->copy_stream));
+  IG_CUDA(cudaEventRecord(pl->ev_copied, pl->copy_stream));
+  pl->prefetched = true;
   return IG_OK;
 }
 
