@@ -15,12 +15,21 @@
 #include <vector>
 
 #include "ig_internal.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace ig;
 
 namespace {
 
 thread_local std::string g_last_error;
+
+// NVTX range around an API call (a no-op unless a profiler is attached), so
+// a profile can be filtered by call and pass, e.g. `ncu --nvtx
+// --nvtx-include "ig pass 4/"`.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 ig_status fail(ig_status st, const std::string& msg) {
   g_last_error = msg;
@@ -507,6 +516,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
                           const ig_tuning* tuning, ig_plan** out) {
   g_last_error.clear();
   if (!out) return fail(IG_EINVAL, "out is NULL");
+  Range range("ig plan");
   *out = nullptr;
   if (!p) return fail(IG_EINVAL, "params is NULL");
   if (p->symbol_bits != 8 && p->symbol_bits != 2) return fail(IG_EINVAL, "symbol_bits must be 8 or 2");
@@ -875,6 +885,9 @@ ig_status intergrams_pass(ig_plan* pl, uint32_t* j_done) {
   if (!pl) return fail(IG_EINVAL, "plan is NULL");
   if (pl->next_j > pl->p.n) return IG_DONE;
   const uint32_t j = pl->next_j;
+  char name[32];
+  std::snprintf(name, sizeof(name), "ig pass %u", j);
+  Range range(name);
   pl->kernels += enqueue_pass(pl, j, pl->stream);
   IG_CUDA(cudaGetLastError());
   finish_pass_host(pl, j);
@@ -885,6 +898,7 @@ ig_status intergrams_pass(ig_plan* pl, uint32_t* j_done) {
 ig_status intergrams_run(ig_plan* pl) {
   g_last_error.clear();
   if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  Range range("ig run");
   if (pl->next_j > pl->p.n) return IG_OK;
   const bool from_start = pl->next_j == pl->b;
   if ((pl->p.flags & IG_F_GRAPH) && from_start) {
@@ -1001,6 +1015,7 @@ ig_status intergrams_topk(ig_plan* pl, uint8_t* keys_out, uint64_t* counts_out, 
 ig_status intergrams_features(ig_plan* pl, uint64_t* row_ptr, uint32_t* cols, uint64_t capacity, uint64_t* nnz_out) {
   g_last_error.clear();
   if (!pl || !nnz_out) return fail(IG_EINVAL, "plan or nnz_out is NULL");
+  Range range("ig features");
   *nnz_out = 0;
   if (pl->dry_run) return fail(IG_ESTATE, "dry-run plan");
   if (pl->last_j != pl->p.n || pl->next_j <= pl->p.n) return fail(IG_ESTATE, "the job's passes have not all run");
