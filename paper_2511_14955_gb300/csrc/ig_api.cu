@@ -228,6 +228,8 @@ void release(ig_plan* pl) {
   if (!pl) return;
   if (pl->graph) cudaGraphExecDestroy(pl->graph);
   if (pl->graph_alt) cudaGraphExecDestroy(pl->graph_alt);
+  // a prefetch copy may still be landing in a buffer freed below
+  if (pl->copy_stream) cudaStreamSynchronize(pl->copy_stream);
   for (cudaEvent_t e : {pl->ev_copied, pl->ev_left[0], pl->ev_left[1]})
     if (e) cudaEventDestroy(e);
   if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
