@@ -327,3 +327,19 @@ def test_invalid_arguments_rejected():
     bad_off[2], bad_off[3] = bad_off[3], bad_off[2]
     with pytest.raises(B.IntergramsError):
         B.Plan(d, dev(data, bad_off)[1], n=4, k=1, candidates=4)
+
+
+@pytest.mark.parametrize("mode", [O.EQ2_ONCE_PER_SEQUENCE, O.EQ1_EVERY_OCCURRENCE])
+def test_maximum_candidate_count(mode):
+    """Z = 2^24 - 1, the largest the ABI takes: sigma * Z slots use the whole
+    32-bit slot range (the highest slot stays below the empty-entry marker).
+    Z covers every prefix of this corpus, so the result is the exhaustive
+    top-k (Algorithm 3 with nothing filtered out)."""
+    data, off, _ = synth.make_corpus("markov_2mb", seed=9, m=6, max_len=8192)
+    d, o = dev(data, off)
+    Z = (1 << 24) - 1
+    with B.Plan(d, o, n=4, k=1000, candidates=Z, base_n=1, count_mode=mode) as pl:
+        pl.run()
+        gk, gc, _ = pl.topk()
+    ek, ec = O.exhaustive(data, off, 4, 1000, count_mode=mode)
+    assert np.array_equal(gk, ek) and np.array_equal(gc, ec)
