@@ -1,7 +1,10 @@
 """Pins for the CPU oracle (no GPU).
 
 The oracle is checked against things other than itself:
-  * brute force (plain Python dictionaries) on tiny corpora, Eq. 1 and Eq. 2;
+  * brute force (plain Python dictionaries) on tiny corpora, Eq. 1 and Eq. 2,
+    for the exhaustive count and for Algorithm 3 with small Z (a selection
+    tie order reversed, one candidate too many, or prefixes taken from the
+    wrong end each fail it on nearly every seed);
   * closed forms: de Bruijn sequences (every n-gram exactly once, so the
     top-k is the k smallest n-grams in byte order - this pins tie-breaking),
     all-zero sequences, periodic sequences;
@@ -64,6 +67,42 @@ def test_exhaustive_matches_brute_force(seed):
             bk, bc = brute_top(seqs, n, k, mode)
             assert keys.tolist() == bk
             assert counts.tolist() == bc
+
+
+def brute_intergrams(seqs, n, k, Z, base_n, mode):
+    """Algorithm 3 restated with Python dictionaries: exact base_n-gram counts,
+    then for j = base_n+1 .. n the j-grams whose (j-1)-prefix is among the
+    previous pass's top-Z, counted exactly; the top-k of the last pass. Every
+    selection orders by count descending, then symbols ascending."""
+    b = min(base_n, n)
+
+    def select(c, t):
+        return [g for g, _ in sorted(c.items(), key=lambda kv: (-kv[1], kv[0]))[:t]]
+
+    counts = brute_counts(seqs, b, mode)
+    for j in range(b + 1, n + 1):
+        kept = set(select(counts, Z))
+        counts = {g: v for g, v in brute_counts(seqs, j, mode).items() if g[:-1] in kept}
+    items = sorted(counts.items(), key=lambda kv: (-kv[1], kv[0]))[:k]
+    return [list(g) for g, _ in items], [v for _, v in items]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_intergrams_matches_brute_force(seed):
+    """Algorithm 3 on tiny corpora with small Z (so the filter removes
+    prefixes and ties decide membership), every base length, both modes."""
+    rng = np.random.default_rng(1000 + seed)
+    sigma = [2, 3, 4, 256][seed % 4]
+    seqs = random_seqs(rng, int(rng.integers(1, 9)), 80, sigma)
+    data, off = corpus(seqs)
+    for n in (2, 3, 5, 6):
+        for base in (1, 2, 3):
+            for mode in (O.EQ2_ONCE_PER_SEQUENCE, O.EQ1_EVERY_OCCURRENCE):
+                Z = int(rng.integers(1, 12))
+                k = int(rng.integers(1, Z + 1))
+                keys, counts = O.intergrams(data, off, n, k, Z, base_n=base, count_mode=mode)
+                bk, bc = brute_intergrams(seqs, n, k, Z, base, mode)
+                assert keys.tolist() == bk and counts.tolist() == bc, (n, base, mode, Z, k)
 
 
 def _pack_by_hand(codes):
