@@ -103,6 +103,10 @@ def test_intergrams_matches_brute_force(seed):
                 keys, counts = O.intergrams(data, off, n, k, Z, base_n=base, count_mode=mode)
                 bk, bc = brute_intergrams(seqs, n, k, Z, base, mode)
                 assert keys.tolist() == bk and counts.tolist() == bc, (n, base, mode, Z, k)
+                if sigma == 4:  # the same corpus packed 2 bits per base
+                    pk, pc = O.intergrams(_pack_by_hand([c for q in seqs for c in q]), off, n, k, Z,
+                                          base_n=base, count_mode=mode, symbol_bits=2)
+                    assert pk.tolist() == bk and pc.tolist() == bc, (n, base, mode, Z, k, "2-bit")
 
 
 def _pack_by_hand(codes):
