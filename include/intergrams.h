@@ -133,6 +133,9 @@ typedef struct {
   uint32_t tile_cache_hint;  /* L2 policy of the corpus tile copies: 1 = none, 2 = evict first (read
                                 once per pass, so the counters, spill lists and tables keep L2);
                                 0 = default (2) */
+  uint32_t l2_hints;         /* L2 policy of the scan's own traffic: 2 = slot counters evict last,
+                                Eq. 2 spill lists and survivor bitmasks evict first (touched once
+                                or twice); 1 = none; 0 = default (1) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;
@@ -301,20 +304,35 @@ ig_status intergrams_timings(ig_plan* pl, float* scan_ms, float* pass_ms, uint32
  *   stream       : cudaStream_t the work is ordered on (not synchronised).
  *   keys_out     : DEVICE buffer of k * ceil(n * symbol_bits / 8) bytes.
  *   counts_out   : DEVICE buffer of k uint64 counts.
- *   rows_out     : DEVICE uint32: number of rows written (min(k, #nonzero)).
+ *   rows_out     : DEVICE uint32: number of rows written (min(k, #nonzero)),
+ *                  0 when status_out reports a failure.
+ *   status_out   : DEVICE int32, written stream-ordered at the end of the
+ *                  call's work: IG_OK, or the failure the device reported -
+ *                  IG_ETIMEOUT (a bounded wait for a corpus tile ran out;
+ *                  the counts are incomplete) or IG_ETABLE_FULL (a dedupe
+ *                  set filled up). On a failure rows_out is 0 and the
+ *                  rows in keys_out/counts_out must be ignored. The return
+ *                  value only covers what the host can see when the work is
+ *                  queued (arguments, launch errors): read status_out after
+ *                  the stream has reached it.
  * Rows are in the same order and format as intergrams_topk after a run with
  * n = base_n. Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors returned at once: IG_EINVAL (NULL pointer, sizes beyond the limits
+ * above, Eq. 1 on 2^32 - 1 or more symbols, whose counts the 32-bit scratch
+ * counters cannot hold), IG_ECUDA (a launch or runtime call failed).
  *
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current): make that first call
- * before any stream capture. Every call reuses the same array, which keeps
- * the previous call's contents (the call clears what must start at zero), so
- * calls whose work overlaps on the GPU - from two streams or two threads -
- * race and give wrong results: serialise them.
+ * Every call looks up the scratch array's device address on the current
+ * device (cudaGetSymbolAddress; the first lookup on a device loads the
+ * library's module there): make the first call on each device before any
+ * stream capture. Every call reuses the same array, which keeps the previous
+ * call's contents (the call clears what must start at zero, and the dedupe
+ * epochs carry over), so calls whose work overlaps on the GPU - from two
+ * streams or two threads - race and give wrong results: serialise them.
  */
 ig_status intergrams_dense_topk_static(const ig_params* p, const void* data, const uint64_t* offsets,
                                        uint32_t m, uint64_t total_symbols, void* stream,
-                                       uint8_t* keys_out, uint64_t* counts_out, uint32_t* rows_out);
+                                       uint8_t* keys_out, uint64_t* counts_out, uint32_t* rows_out,
+                                       int32_t* status_out);
 
 /* ------------------------------------------------------------------ serving
  * A server runs many top-k jobs on one GPU with continuous batching: a
@@ -385,9 +403,11 @@ ig_status intergrams_test_fail_alloc(uint32_t nth, uint64_t* live_out);
  * wait (about one second) runs out, the CTA stops, and the pass returns
  * IG_ETIMEOUT (the scan's results are then incomplete; free the plan). The
  * device and other plans stay usable. Chain passes stage no tiles and are
- * unaffected.
- * Errors: IG_EINVAL (NULL plan), IG_ESTATE (plan made with IG_F_GRAPH, whose
- * captured launches the hook cannot reach).
+ * unaffected. With pl = NULL the hook arms the next call of
+ * intergrams_dense_topk_static instead (once): its scan stalls the same way
+ * and the call reports IG_ETIMEOUT through its status_out word.
+ * Errors: IG_ESTATE (plan made with IG_F_GRAPH, whose captured launches the
+ * hook cannot reach).
  */
 ig_status intergrams_test_stall_tiles(ig_plan* pl);
 

@@ -43,7 +43,7 @@ class IgTuning(ctypes.Structure):
                 ("ctas_per_sm", "threads", "words_per_thread", "smem_set_log2", "table_load_pct", "hot_log2",
                  "chain_from", "list_pct", "log_mode", "log_pct", "log_chunk_log2", "log_range_log2",
                  "dedupe_bitmap", "dense_prefix", "base_words_per_thread", "base_smem_set_log2",
-                 "set_probes", "tile_buffers", "rs_depth", "tile_cache_hint")]
+                 "set_probes", "tile_buffers", "rs_depth", "tile_cache_hint", "l2_hints")]
 
 
 class IgPassStats(ctypes.Structure):
@@ -107,7 +107,8 @@ def load(build_if_missing: bool = True):
     lib.intergrams_free.restype = None
     lib.intergrams_free.argtypes = [P]
     lib.intergrams_dense_topk_static.restype = ctypes.c_int
-    lib.intergrams_dense_topk_static.argtypes = [ctypes.POINTER(IgParams), P, P, U32, ctypes.c_uint64, P, P, P, P]
+    lib.intergrams_dense_topk_static.argtypes = [ctypes.POINTER(IgParams), P, P, U32, ctypes.c_uint64, P, P, P, P,
+                                                 P]
     lib.intergrams_plan_device_bytes.restype = ctypes.c_int
     lib.intergrams_plan_device_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
     lib.intergrams_server_create.restype = ctypes.c_int
@@ -298,13 +299,15 @@ def test_fail_alloc(nth: int) -> int:
 
 def dense_topk_static(data, offsets, *, n: int, k: int, symbol_bits: int = 8,
                       count_mode: int = COUNT_ONCE_PER_SEQUENCE, total_symbols: int, stream=None,
-                      keys_out=None, counts_out=None, rows_out=None):
+                      keys_out=None, counts_out=None, rows_out=None, status_out=None):
     """Allocation-free exact top-k of short n-grams (intergrams_dense_topk_static).
 
     ``data``/``offsets`` are CUDA tensors; ``keys_out`` (uint8, k * row bytes),
-    ``counts_out`` (int64, k) and ``rows_out`` (int32, 1) are caller-owned CUDA
-    tensors. The library allocates nothing; the work is enqueued on ``stream``
-    (default: torch's current stream) and not synchronised.
+    ``counts_out`` (int64, k), ``rows_out`` (int32, 1) and ``status_out``
+    (int32, 1) are caller-owned CUDA tensors. The library allocates nothing;
+    the work is enqueued on ``stream`` (default: torch's current stream) and
+    not synchronised: ``status_out`` holds IG_OK or the device-side failure
+    (then ``rows_out`` is 0) once the stream has reached it.
     """
     lib = load()
     m = len(offsets) - 1
@@ -315,8 +318,17 @@ def dense_topk_static(data, offsets, *, n: int, k: int, symbol_bits: int = 8,
     else:
         stream_ptr = getattr(stream, "cuda_stream", stream)
     st = lib.intergrams_dense_topk_static(ctypes.byref(params), _ptr(data), _ptr(offsets), m, int(total_symbols),
-                                          stream_ptr, _ptr(keys_out), _ptr(counts_out), _ptr(rows_out))
+                                          stream_ptr, _ptr(keys_out), _ptr(counts_out), _ptr(rows_out),
+                                          _ptr(status_out))
     _check(lib, st, "intergrams_dense_topk_static")
+
+
+def test_stall_next_static_call():
+    """Test hook: the next dense_topk_static call's scan waits for tiles that
+    are never sent, so its status word reports IG_ETIMEOUT after about a
+    second (intergrams_test_stall_tiles with no plan)."""
+    lib = load()
+    _check(lib, lib.intergrams_test_stall_tiles(None), "intergrams_test_stall_tiles")
 
 
 class Server:

@@ -135,6 +135,7 @@ struct ScanArgs {
   uint32_t tile2;              // word offset of the second tile buffer in dynamic smem (0 = one buffer)
   uint32_t stall_tiles;        // test hook: tile barriers are never armed, so tile waits run out
   uint32_t tile_evict_first;   // corpus tile copies carry an L2 evict-first policy
+  uint32_t l2_hints;           // counters evict-last, spill lists and survivor bitmasks evict-first
   PassCtl* ctl;
 };
 
@@ -156,6 +157,10 @@ void launch_features(const uint8_t* data, uint64_t data_bytes, const uint64_t* o
                      unsigned long long* keys, uint4* table, uint32_t table_log2, uint32_t* queue, uint32_t* status,
                      uint32_t* row_nnz, uint64_t* row_ptr, uint32_t* cols, bool count, int grid,
                      uint32_t words_per_thread, uint32_t tile_words, size_t smem, cudaStream_t s);
+
+// Test hook of the allocation-free entry point (ig_noalloc.cu): its next
+// call's scan waits for tiles that are never sent.
+void arm_static_stall();
 
 // Count the registration log of the pass just scanned: one launch per counter
 // range, so the counters being incremented at any time span one range.

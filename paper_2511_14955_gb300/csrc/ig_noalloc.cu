@@ -14,7 +14,7 @@
 // Nothing here is allocated: no cudaMalloc, cudaFree, host-pinned memory or
 // allocating library routine. The scratch array occupies kScratchBytes on
 // every GPU that loads the library, until the process exits.
-#include <mutex>
+#include <atomic>
 
 #include "ig_internal.cuh"
 
@@ -29,8 +29,12 @@ constexpr uint32_t kThreads = 512, kWords = 9, kSsetLog2 = 15;
 constexpr uint32_t kGsetLog2 = 17;                   // >= 2 * kMaxSlots entries per CTA set
 
 // Host code must not take this array's address directly (the host-side name
-// is only a stand-in); it asks the runtime for the device address once per
-// device and passes that pointer to the kernels.
+// is only a stand-in); every call asks the runtime for the device address on
+// the current device (cheap, allocates nothing) and passes that pointer to
+// the kernels, so a context made again after a device reset is followed.
+// The array starts zeroed when the module loads; the control block's dedupe
+// epochs carry over from call to call, so the dedupe sets are cleared only
+// when the 32-bit epochs wrap.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct Layout {
@@ -64,12 +68,26 @@ __global__ void iota_kernel(uint32_t* order, uint32_t m) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) order[i] = i;
 }
 
-__global__ void rows_kernel(const PassCtl* ctl, uint32_t k, uint32_t* rows) {
-  if (threadIdx.x == 0) rows[0] = ctl->nsel < k ? ctl->nsel : k;
+// Start of a call: the sticky status bits of the previous call are dropped
+// (the dedupe epochs are kept).
+__global__ void clear_status_kernel(PassCtl* ctl) {
+  if (threadIdx.x == 0) ctl->status = 0;
 }
 
-std::mutex g_mu;
-void* g_dev_ptr[64] = {};  // device address of g_scratch, per device
+// End of a call: the row count, or 0 rows and the failure when the scan
+// reported one (a tile wait that ran out, a full dedupe set).
+__global__ void finish_kernel(const PassCtl* ctl, uint32_t k, uint32_t* rows, int32_t* status) {
+  if (threadIdx.x != 0) return;
+  const uint32_t st = ctl->status;
+  int32_t code = IG_OK;
+  if (st & kStTimeout) code = IG_ETIMEOUT;
+  else if (st & kStCountOverflow) code = IG_EOVERFLOW;
+  else if (st & (kStSetFull | kStTableFull | kStListFull | kStQueue)) code = IG_ETABLE_FULL;
+  rows[0] = code != IG_OK ? 0u : (ctl->nsel < k ? ctl->nsel : k);
+  status[0] = code;
+}
+
+std::atomic<uint32_t> g_stall_next{0};  // test hook: the next call's tile waits run out
 
 }  // namespace
 
@@ -82,13 +100,14 @@ using namespace ig;
 
 extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void* data, const uint64_t* offsets,
                                                   uint32_t m, uint64_t total_symbols, void* stream,
-                                                  uint8_t* keys_out, uint64_t* counts_out, uint32_t* rows_out) {
+                                                  uint8_t* keys_out, uint64_t* counts_out, uint32_t* rows_out,
+                                                  int32_t* status_out) {
   auto bad = [&](ig_status st, const char* msg) {
     set_last_error(msg);
     return st;
   };
   set_last_error("");
-  if (!p || !offsets || !keys_out || !counts_out || !rows_out) return bad(IG_EINVAL, "NULL argument");
+  if (!p || !offsets || !keys_out || !counts_out || !rows_out || !status_out) return bad(IG_EINVAL, "NULL argument");
   if (p->symbol_bits != 8 && p->symbol_bits != 2) return bad(IG_EINVAL, "symbol_bits must be 8 or 2");
   if (p->count_mode > 1) return bad(IG_EINVAL, "count_mode must be 0 or 1");
   if (p->n < 1 || p->n * p->symbol_bits > 16)
@@ -96,23 +115,14 @@ extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void
   if (p->k < 1 || p->k > kMaxSlots) return bad(IG_EINVAL, "k must be in 1..65536");
   if (m > kMaxSeqs) return bad(IG_EINVAL, "too many sequences for the static scratch (limit 2^20)");
   if (total_symbols && !data) return bad(IG_EINVAL, "data is NULL");
+  if (p->count_mode == IG_COUNT_EVERY_OCCURRENCE && total_symbols >= 0xFFFFFFFFull)
+    return bad(IG_EINVAL, "Eq. 1 counts of 2^32 - 1 or more windows do not fit the 32-bit counters of the static scratch");
   const Layout L = layout();
   if (L.end > kScratchBytes) return bad(IG_EINVAL, "internal: scratch layout exceeds its array");
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return bad(IG_ECUDA, "cudaGetDevice failed");
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
-      cudaError_t e = cudaGetSymbolAddress(&g_dev_ptr[dev], g_scratch);
-      if (e != cudaSuccess) {
-        g_dev_ptr[dev] = nullptr;
-        return bad(IG_ECUDA, "cudaGetSymbolAddress(g_scratch) failed");
-      }
-    }
-    base = g_dev_ptr[dev];
-  }
+  if (cudaGetSymbolAddress(&base, g_scratch) != cudaSuccess || !base)
+    return bad(IG_ECUDA, "cudaGetSymbolAddress(g_scratch) failed");
   unsigned char* S = static_cast<unsigned char*>(base);
   PassCtl* ctl = reinterpret_cast<PassCtl*>(S + L.ctl);
   uint32_t* counts = reinterpret_cast<uint32_t*>(S + L.counts);
@@ -129,15 +139,15 @@ extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void
   const size_t smem = ((size_t)4 << kSsetLog2) + (size_t)tile_words * 4;
   if (scan_raise_smem_limit(sb, true, smem) != cudaSuccess) return bad(IG_ECUDA, "cudaFuncSetAttribute failed");
 
-  // the scratch keeps the previous call's contents: zero what must start at 0
-  if (cudaMemsetAsync(ctl, 0, sizeof(PassCtl), s) != cudaSuccess) return bad(IG_ECUDA, "cudaMemsetAsync failed");
-  if (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE &&
-      cudaMemsetAsync(gset, 0, sizeof(unsigned long long) * ((size_t)kGrid << kGsetLog2), s) != cudaSuccess)
-    return bad(IG_ECUDA, "cudaMemsetAsync failed");
+  // the scratch keeps the previous call's contents: zero what must start at
+  // 0 (status bits, counters); the dedupe sets are cleared when the epochs
+  // carried over from earlier calls would wrap
+  clear_status_kernel<<<1, 32, 0, s>>>(ctl);
   if (m) iota_kernel<<<256, 256, 0, s>>>(reinterpret_cast<uint32_t*>(S + L.order), m);
-
-  launch_pass_reset(ctl, m, nullptr, 0, s);
-  cudaMemsetAsync(counts, 0, nslots * sizeof(uint32_t), s);
+  launch_pass_reset(ctl, m, p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE ? gset : nullptr,
+                    (uint64_t)kGrid << kGsetLog2, s);
+  if (cudaMemsetAsync(counts, 0, nslots * sizeof(uint32_t), s) != cudaSuccess)
+    return bad(IG_ECUDA, "cudaMemsetAsync failed");
   ScanArgs a{};
   a.data = static_cast<const uint8_t*>(data);
   a.data_bytes = (total_symbols * sb + 7) / 8;
@@ -155,7 +165,8 @@ extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void
   a.words_per_thread = kWords;
   a.sset_log2 = kSsetLog2;
   a.tile_words = tile_words;
-  a.check_overflow = (p->count_mode == IG_COUNT_EVERY_OCCURRENCE && total_symbols >= 0xFFFFFFFFull) ? 1u : 0u;
+  a.check_overflow = 0;  // Eq. 1 inputs of 2^32 - 1 or more windows are rejected above
+  a.stall_tiles = g_stall_next.exchange(0);
   a.ctl = ctl;
   if (m) launch_scan(a, sb, true, (int)kGrid, (int)kThreads, smem, s);
   launch_select(counts, false, nullptr, sb, nslots, p->k, ctl, reinterpret_cast<uint32_t*>(S + L.hist),
@@ -168,8 +179,12 @@ extern "C" ig_status intergrams_dense_topk_static(const ig_params* p, const void
   launch_write_topk(reinterpret_cast<uint32_t*>(S + L.sel_slot), 0, n, reinterpret_cast<uint32_t*>(S + L.sel_count),
                     reinterpret_cast<uint32_t*>(S + L.idx0), ctl, sb, n, (n * sb + 7) / 8, p->k, keys_out,
                     reinterpret_cast<unsigned long long*>(counts_out), s);
-  rows_kernel<<<1, 32, 0, s>>>(ctl, p->k, rows_out);
+  finish_kernel<<<1, 32, 0, s>>>(ctl, p->k, rows_out, status_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bad(IG_ECUDA, cudaGetErrorString(e));
   return IG_OK;
 }
+
+// Test hook behind intergrams_test_stall_tiles(NULL): the next call's scan
+// waits for tiles that are never sent.
+void ig::arm_static_stall() { g_stall_next.store(1); }
