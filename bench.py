@@ -51,6 +51,10 @@ def parse_args(argv=None):
     ap.add_argument("--serve-jobs", type=int, default=120, help="jobs in the serving leg (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--count-mode", type=int, choices=[0, 1], default=0,
+                    help="0 = once per sequence (Eq. 2, the headline), 1 = every occurrence (Eq. 1)")
+    ap.add_argument("--tuning", default=None,
+                    help='JSON object of tuning knobs (include/intergrams.h ig_tuning) fixed before autotuning')
     return ap.parse_args(argv)
 
 
@@ -155,6 +159,14 @@ def job_params(name: str):
     from paper_2511_14955_gb300 import synth
     w = synth.WORKLOADS[name]
     return dict(n=w.n, k=w.k, candidates=w.candidates, base_n=w.base_n, symbol_bits=w.symbol_bits)
+
+
+def per_pass_median(ms, npass):
+    """Median over steps of each pass's time (ms lists the passes of every
+    step in order)."""
+    if not ms or npass <= 0:
+        return []
+    return [round(statistics.median(ms[i::npass]), 3) for i in range(npass)]
 
 
 def passes_of(p) -> int:
@@ -311,6 +323,7 @@ def main(argv=None):
     torch.cuda.set_device(dev)
 
     p = job_params(args.workload)
+    p["count_mode"] = args.count_mode
     w = synth.WORKLOADS[args.workload]
     seed = rank_seed(args.seed, rank)
     L = synth.lengths_for(w, seed, args.m)
@@ -327,7 +340,9 @@ def main(argv=None):
     torch.cuda.synchronize(dev)
 
     npass = passes_of(p)
-    plan = binding.Plan(d_data, d_off, **p, graph=True, timing=True, autotune=not args.no_autotune, stream=stream)
+    tuning = json.loads(args.tuning) if args.tuning else None
+    plan = binding.Plan(d_data, d_off, **p, graph=True, timing=True, autotune=not args.no_autotune, stream=stream,
+                        tuning=tuning)
 
     def barrier():
         if world > 1:
@@ -348,7 +363,7 @@ def main(argv=None):
 
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
-    scan_ms, launches = [], 0
+    scan_ms, pass_ms, launches = [], [], 0
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -357,8 +372,9 @@ def main(argv=None):
         plan.rewind()
         plan.run()
         plan.topk()
-        s_ms, _, kern = plan.timings()
+        s_ms, p_ms, kern = plan.timings()
         scan_ms.extend(float(x) for x in s_ms)
+        pass_ms.append([float(x) for x in p_ms])
         launches += kern
     ev1.record(stream)
     barrier()
@@ -384,7 +400,7 @@ def main(argv=None):
     # is started (intergrams_prefetch) while the step before it runs
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(5, args.steps))
     hplan = binding.Plan(host.numpy()[:nbytes], off, **p, graph=True, host_input=True, stream=stream,
-                         autotune=not args.no_autotune)  # the knobs the device plan got (cached)
+                         autotune=not args.no_autotune, tuning=tuning)  # the knobs the device plan got (cached)
     hplan.run()
     hplan.topk()
     barrier()
@@ -426,7 +442,8 @@ def main(argv=None):
         "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": args.workload, "m": len(L), "corpus_bytes": nbytes, **p,
-                   "count_mode": "once_per_sequence (Eq. 2)", "passes": npass,
+                   "count_mode": ("once_per_sequence (Eq. 2)" if args.count_mode == 0
+                                  else "every_occurrence (Eq. 1)"), "passes": npass,
                    "launch": "one persistent scan per pass, CUDA graph per job",
                    "l2": "inputs larger than L2 (corpus 8.4 GB vs 129 MB L2)",
                    "parallelism": f"independent jobs x{world}"},
@@ -438,7 +455,9 @@ def main(argv=None):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "scan_kernel (corpus scan of one pass)",
-                     "peak_kind": f"{peak_kind} hbm_gbs", "avg_scan_ms": avg_scan_s * 1e3},
+                     "peak_kind": f"{peak_kind} hbm_gbs", "avg_scan_ms": avg_scan_s * 1e3,
+                     "scan_ms_per_pass": per_pass_median(scan_ms, npass),
+                     "pass_ms_per_pass": per_pass_median([x for r in pass_ms for x in r], npass)},
         "clocks": clk,
     }
     if features:

@@ -133,9 +133,6 @@ typedef struct {
   uint32_t tile_cache_hint;  /* L2 policy of the corpus tile copies: 1 = none, 2 = evict first (read
                                 once per pass, so the counters, spill lists and tables keep L2);
                                 0 = default (2) */
-  uint32_t l2_hints;         /* L2 policy of the scan's own traffic: 2 = slot counters evict last,
-                                Eq. 2 spill lists and survivor bitmasks evict first (touched once
-                                or twice); 1 = none; 0 = default (1) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

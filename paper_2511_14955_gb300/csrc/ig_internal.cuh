@@ -135,7 +135,6 @@ struct ScanArgs {
   uint32_t tile2;              // word offset of the second tile buffer in dynamic smem (0 = one buffer)
   uint32_t stall_tiles;        // test hook: tile barriers are never armed, so tile waits run out
   uint32_t tile_evict_first;   // corpus tile copies carry an L2 evict-first policy
-  uint32_t l2_hints;           // counters evict-last, spill lists and survivor bitmasks evict-first
   PassCtl* ctl;
 };
 
