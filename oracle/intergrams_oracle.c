@@ -282,6 +282,44 @@ int oracle_intergrams(const uint8_t* data, const uint64_t* offsets, uint32_t m, 
   return rc;
 }
 
+/*
+ * One counting step of Algorithm 3 on its own (Sec. 7): the j-grams of the
+ * corpus whose (j-1)-prefix is one of `prefixes` (nprefix rows of j-1 symbol
+ * codes in ascending order; every j-gram when use_prefixes is 0, the dense
+ * pass of Algorithm 2), counted by Eq. 1 (count_mode 1) or Eq. 2 (count_mode
+ * 0). Writes every distinct counted j-gram with its count, in ascending
+ * symbol order: keys_out (capacity rows of j codes), counts_out. *nout is
+ * always the number of distinct j-grams; OR_EINVAL when it exceeds capacity.
+ *
+ * Sequences are independent under both equations, so the counts of a corpus
+ * split into groups of whole sequences are the sums of the groups' counts;
+ * the test harness uses this to run the oracle on several cores.
+ */
+int oracle_count_pass(const uint8_t* data, const uint64_t* offsets, uint32_t m, uint32_t symbol_bits, uint32_t j,
+                      uint32_t count_mode, const uint8_t* prefixes, uint64_t nprefix, uint32_t use_prefixes,
+                      uint8_t* keys_out, uint64_t* counts_out, uint64_t capacity, uint64_t* nout) {
+  *nout = 0;
+  if (j == 0 || (use_prefixes && j < 2) || !valid_corpus(offsets, m, symbol_bits)) return OR_EINVAL;
+  uint8_t* sym = unpack_symbols(data, offsets[m], symbol_bits);
+  if (!sym) return OR_ENOMEM;
+  key_set P = {(uint8_t*)prefixes, nprefix, j - 1};
+  gram_count* gc = NULL;
+  uint64_t nd = 0;
+  int rc = count_grams(sym, offsets, m, j, count_mode, use_prefixes ? &P : NULL, &gc, &nd);
+  if (rc == OR_OK) {
+    *nout = nd;
+    if (nd > capacity) {
+      rc = OR_EINVAL;
+    } else {
+      /* count_grams leaves the distinct j-grams in ascending symbol order */
+      write_top(sym, gc, nd, j, keys_out, counts_out);
+    }
+  }
+  free(gc);
+  free(sym);
+  return rc;
+}
+
 /* ----------------------------------------------------- counting given keys */
 
 static uint8_t symbol_at(const uint8_t* data, uint32_t symbol_bits, uint64_t g) {

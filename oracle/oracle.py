@@ -11,6 +11,9 @@ Functions follow the paper directly:
   Sec. 3: every n-gram is counted, sorted by count, the top k kept.
 * :func:`intergrams` - Algorithm 3 (Sec. 7), with Algorithm 2 (Sec. 6) as
   its first pass generalised to a base length ``base_n``.
+* :func:`count_pass` - one counting step of Algorithm 3 on its own (used by
+  ``oracle/sharded.py`` to run the oracle over groups of whole sequences on
+  several cores).
 
 Output keys are returned as an ``(r, n)`` uint8 array of symbol codes (one
 code per symbol; for 2-bit data the codes are 0..3) and the counts as a
@@ -58,6 +61,8 @@ def _load():
         lib.oracle_intergrams.argtypes = [P, P, U32, U32, U32, U32, U64, U32, U64, U32, P, P, P, P]
         lib.oracle_count_keys.restype = ctypes.c_int
         lib.oracle_count_keys.argtypes = [P, P, U32, U32, U32, U32, P, U64, P]
+        lib.oracle_count_pass.restype = ctypes.c_int
+        lib.oracle_count_pass.argtypes = [P, P, U32, U32, U32, U32, P, U64, U32, P, P, U64, P]
         lib.oracle_features.restype = ctypes.c_int
         lib.oracle_features.argtypes = [P, P, U32, U32, U32, P, U32, P, P, U64, P]
         _lib = lib
@@ -114,6 +119,36 @@ def intergrams(data, offsets, n: int, k: int, candidates: int, base_n: int = 3,
     if want_survivors:
         return keys[:r].copy(), counts[:r].copy(), surv.value
     return keys[:r].copy(), counts[:r].copy()
+
+
+def count_pass(data, offsets, j: int, prefixes=None, count_mode: int = EQ2_ONCE_PER_SEQUENCE,
+               symbol_bits: int = 8):
+    """One counting step of Algorithm 3: every distinct j-gram whose
+    (j-1)-prefix is a row of ``prefixes`` (an (r, j-1) uint8 array of symbol
+    codes in ascending order; None = every j-gram, the dense pass) with its
+    Eq. 2 (or Eq. 1) count. Returns (keys (d, j) uint8 ascending, counts
+    uint64[d])."""
+    lib = _load()
+    data, offsets, m = _prep(data, offsets)
+    use = prefixes is not None
+    pre = np.ascontiguousarray(np.asarray(prefixes if use else np.zeros((1, 1)), dtype=np.uint8))
+    npre = pre.shape[0] if use else 0
+    if use and npre == 0:
+        pre = np.zeros((1, max(j - 1, 1)), np.uint8)
+    cap = 1 << 16
+    while True:
+        keys = np.zeros((cap, j), np.uint8)
+        counts = np.zeros(cap, np.uint64)
+        nout = ctypes.c_uint64(0)
+        rc = lib.oracle_count_pass(data.ctypes.data, offsets.ctypes.data, m, symbol_bits, j, count_mode,
+                                   pre.ctypes.data, npre, 1 if use else 0, keys.ctypes.data, counts.ctypes.data,
+                                   cap, ctypes.byref(nout))
+        d = nout.value
+        if rc == 0:
+            return keys[:d].copy(), counts[:d].copy()
+        if d <= cap:
+            raise ValueError(f"oracle_count_pass failed: {rc}")
+        cap = int(d)
 
 
 def count_keys(data, offsets, keys, count_mode: int = EQ2_ONCE_PER_SEQUENCE, symbol_bits: int = 8):

@@ -385,3 +385,80 @@ def test_feature_column_sums_are_eq2_counts(bits):
         row_ptr, cols = O.features(data, off, keys, symbol_bits=bits)
         assert np.bincount(cols, minlength=len(keys)).tolist() == counts.tolist()
         assert all(np.all(np.diff(cols[row_ptr[i]:row_ptr[i + 1]].astype(np.int64)) > 0) for i in range(len(seqs)))
+
+
+# --------------------------------------------------------------- one pass alone
+
+@pytest.mark.parametrize("seed", range(12))
+def test_count_pass_matches_brute_force(seed):
+    """One counting step of Algorithm 3 with a given prefix set equals a
+    dictionary count of the j-grams whose (j-1)-prefix is in the set."""
+    rng = np.random.default_rng(1000 + seed)
+    sigma = [2, 4, 256][seed % 3]
+    seqs = random_seqs(rng, int(rng.integers(1, 7)), 40, sigma)
+    data, off = corpus(seqs)
+    mode = seed % 2
+    j = int(rng.integers(2, 5))
+    prev = sorted(brute_counts(seqs, j - 1, mode))
+    keep = [g for g in prev if rng.random() < 0.5]
+    pre = np.array(keep, np.uint8).reshape(len(keep), j - 1)
+    keys, counts = O.count_pass(data, off, j, pre, count_mode=mode)
+    want = {g: c for g, c in brute_counts(seqs, j, mode).items() if g[:-1] in set(keep)}
+    assert [tuple(r) for r in keys] == sorted(want)            # ascending symbol order
+    assert [int(c) for c in counts] == [want[g] for g in sorted(want)]
+    # no prefix set: the dense pass over every j-gram
+    keys, counts = O.count_pass(data, off, j, None, count_mode=mode)
+    want = brute_counts(seqs, j, mode)
+    assert [tuple(r) for r in keys] == sorted(want)
+    assert [int(c) for c in counts] == [want[g] for g in sorted(want)]
+
+
+# ------------------------------------------- the oracle over groups of sequences
+
+def _sharded():
+    from oracle import sharded
+    return sharded
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("workers", [1, 2, 5])
+def test_sharded_equals_single_threaded_oracle(mode, workers):
+    """The harness that runs the counting step over groups of whole sequences
+    on several cores, sums the counts and selects between passes gives the
+    single-threaded oracle's rows after every pass (ties included: Z and k cut
+    through runs of equal counts)."""
+    S = _sharded()
+    rng = np.random.default_rng(7 + workers + 10 * mode)
+    seqs = [list(rng.integers(0, 6, size=int(rng.integers(0, 400)))) for _ in range(9)] + [[], [1, 2]]
+    data, off = corpus(seqs)
+    out = S.intergrams(data, off, 6, 40, 60, base_n=2, count_mode=mode, workers=workers, per_pass=True)
+    assert [j for j, _, _ in out] == [2, 3, 4, 5, 6]
+    for j, keys, counts in out:
+        ek, ec = O.intergrams(data, off, 6, 40, 60, base_n=2, count_mode=mode, stop_j=j)
+        assert np.array_equal(keys, ek) and np.array_equal(counts, ec), j
+
+
+def test_sharded_two_bit_and_long_keys():
+    """2-bit input split at sequence starts that fall inside a byte, and keys
+    longer than 8 symbols (compared as byte rows)."""
+    S = _sharded()
+    rng = np.random.default_rng(3)
+    codes = [list(rng.integers(0, 4, size=int(rng.integers(5, 300)))) for _ in range(7)]
+    flat = [c for s in codes for c in s]
+    pad = (-len(flat)) % 4
+    f = np.array(flat + [0] * pad, np.uint8).reshape(-1, 4)
+    data = ((f[:, 0] << 6) | (f[:, 1] << 4) | (f[:, 2] << 2) | f[:, 3]).astype(np.uint8)
+    _, off = corpus(codes)
+    for n, base in ((11, 4), (6, 6)):
+        ek, ec = O.intergrams(data, off, n, 30, 50, base_n=base, symbol_bits=2)
+        gk, gc = S.intergrams(data, off, n, 30, 50, base_n=base, symbol_bits=2, workers=3)
+        assert np.array_equal(gk, ek) and np.array_equal(gc, ec)
+
+
+def test_shard_bounds_cover_every_sequence_once():
+    S = _sharded()
+    off = np.cumsum([0, 5, 0, 100, 1, 1, 7, 0, 300]).astype(np.uint64)
+    for g in (1, 2, 3, 8, 20):
+        b = S.shard_bounds(off, g)
+        assert b[0][0] == 0 and b[-1][1] == len(off) - 1
+        assert all(x[1] == y[0] for x, y in zip(b, b[1:])) and all(a < e for a, e in b)
