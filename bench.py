@@ -46,7 +46,11 @@ def parse_args(argv=None):
     ap.add_argument("--max-len", type=int, default=None,
                     help="clamp sequence lengths (small cases for profiler captures)")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--cpu-seqs", type=int, default=24, help="sequences in the oracle's timed sample")
+    ap.add_argument("--cpu-mb", type=float, default=24.0,
+                    help="MB of the workload in the all-core oracle's timed sample")
+    ap.add_argument("--cpu-single-mb", type=float, default=8.0,
+                    help="MB of the workload in the single-core oracle's timed sample")
+    ap.add_argument("--ref-mb", type=float, default=6.0, help="MB of the workload per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=120, help="jobs in the serving leg (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -173,25 +177,46 @@ def passes_of(p) -> int:
     return p["n"] - min(p["base_n"], p["n"]) + 1
 
 
-def cpu_baseline(name: str, seed: int, nseq: int, p):
-    """The CPU oracle (single-threaded, as it stands) on the first `nseq`
-    sequences of the same seeded workload, same parameters."""
-    import numpy as np
-    from oracle import oracle
+def _sample_corpus(name: str, seed: int, nbytes: int):
+    """The first sequences of the seeded workload, up to about `nbytes`
+    symbols (at least one sequence)."""
     from paper_2511_14955_gb300 import synth
+    import numpy as np
     w = synth.WORKLOADS[name]
-    L = synth.lengths_for(w, seed)[:nseq]
-    off = synth.offsets_from_lengths(L)
-    data = synth.fill(w.model, seed, off, w.symbol_bits)
-    nbytes = int(data.size)
+    L = synth.lengths_for(w, seed)
+    keep = max(1, int(np.searchsorted(np.cumsum(L.astype(np.int64)), nbytes, side="right")))
+    off = synth.offsets_from_lengths(L[:keep])
+    return synth.fill(w.model, seed, off, w.symbol_bits), off, keep
+
+
+def _oracle_run(name, seed, p, nbytes, workers):
+    """Time the oracle's whole job on a sample; GB/s per pass as the metric."""
+    from oracle import oracle, sharded
+    data, off, keep = _sample_corpus(name, seed, nbytes)
+    args = dict(base_n=p["base_n"], count_mode=p.get("count_mode", 0), symbol_bits=p["symbol_bits"])
     t0 = time.perf_counter()
-    oracle.intergrams(data, off, p["n"], p["k"], p["candidates"], base_n=p["base_n"],
-                      symbol_bits=p["symbol_bits"])
+    if workers > 1:
+        sharded.intergrams(data, off, p["n"], p["k"], p["candidates"], workers=workers, **args)
+    else:
+        oracle.intergrams(data, off, p["n"], p["k"], p["candidates"], **args)
     dt = time.perf_counter() - t0
-    value = nbytes * passes_of(p) / dt / 1e9
-    sample = (f"first {nseq} sequences of {name} (seed {seed}, {nbytes / 1e6:.1f} MB), full job "
-              f"n={p['n']} k={p['k']} Z={p['candidates']} base_n={p['base_n']}, {dt:.1f} s")
-    return {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample}, np
+    size = int(data.size)
+    sample = (f"first {keep} sequences of {name} (seed {seed}, {size / 1e6:.1f} MB), full job n={p['n']} "
+              f"k={p['k']} Z={p['candidates']} base_n={p['base_n']}, {dt:.1f} s on {workers} core(s)")
+    return size * passes_of(p) / dt / 1e9, sample
+
+
+def cpu_baseline(name: str, seed: int, p, all_bytes: int, single_bytes: int):
+    """The CPU oracle as it stands, timed on the host: on every core (the
+    oracle's counting step over groups of whole sequences in one process per
+    core, counts summed exactly; oracle/sharded.py) and on one core (the
+    single-threaded oracle), each on a bounded sample of the same seeded
+    workload with the same parameters."""
+    cores = os.cpu_count() or 1
+    value, sample = _oracle_run(name, seed, p, all_bytes, cores)
+    single, single_sample = _oracle_run(name, seed, p, single_bytes, 1)
+    return {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "single_core": {"value": single, "unit": "GB/s", "cores": 1, "sample": single_sample}}
 
 
 def _job_topk(d, o, *, n, k, Z, base_n, count_mode):
@@ -281,24 +306,27 @@ def serving_leg(args, seed):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (no reference implementation exists),
+    on every host core, each step a bounded sample of the same workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     p = job_params(args.workload)
-    nseq = max(2, args.cpu_seqs // 4)
-    vals = []
+    p["count_mode"] = args.count_mode
+    cores = os.cpu_count() or 1
+    vals, sample = [], ""
     for i in range(args.warmup + args.steps):
-        cb, _ = cpu_baseline(args.workload, args.seed, nseq, p)
+        v, sample = _oracle_run(args.workload, args.seed, p, int(args.ref_mb * 1e6), cores)
         if i >= args.warmup:
-            vals.append(cb)
-    value = statistics.median(v["value"] for v in vals)
+            vals.append(v)
+    value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": "scanned GB/s per pass (n=8,k=64K)", "value": value, "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, **p},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": vals[-1]["sample"]},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -465,8 +493,8 @@ def main(argv=None):
     if args.serve_jobs and world == 1:
         line["serving"] = serving_leg(args, seed)
     if not args.no_cpu_baseline and world == 1:
-        cb, _ = cpu_baseline(args.workload, seed, args.cpu_seqs, p)
-        line["cpu_baseline"] = cb
+        line["cpu_baseline"] = cpu_baseline(args.workload, seed, p, int(args.cpu_mb * 1e6),
+                                            int(args.cpu_single_mb * 1e6))
         # recall of the candidate filter, measured with the library alone
         line["recall"] = recall_leg(seed)
     print(json.dumps(line), flush=True)

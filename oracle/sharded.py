@@ -27,29 +27,36 @@ import numpy as np
 from oracle import oracle as _oracle
 
 
-def shard_bounds(offsets, groups: int):
-    """Contiguous sequence ranges [a, b) of about equal total length (symbols),
-    one per group (fewer when there are fewer sequences)."""
-    off = np.asarray(offsets, dtype=np.uint64).astype(np.int64)
-    m = len(off) - 1
+def shard_groups(offsets, groups: int):
+    """Sequence indices split into at most `groups` groups of about equal
+    total length: longest sequence first, each to the group with the fewest
+    symbols so far (greedy by bytes). Every sequence is in exactly one group,
+    in ascending order within it."""
+    L = np.diff(np.asarray(offsets, dtype=np.uint64).astype(np.int64))
+    m = len(L)
     groups = max(1, min(int(groups), max(m, 1)))
-    total = int(off[-1])
-    cuts = [0]
-    for g in range(1, groups):
-        c = int(np.searchsorted(off, total * g // groups, side="left"))
-        cuts.append(min(max(c, cuts[-1]), m))
-    cuts.append(m)
-    return [(cuts[i], cuts[i + 1]) for i in range(len(cuts) - 1) if cuts[i + 1] > cuts[i]] or [(0, m)]
+    load = np.zeros(groups, np.int64)
+    members = [[] for _ in range(groups)]
+    for i in np.argsort(-L, kind="stable"):
+        g = int(np.argmin(load))
+        members[g].append(int(i))
+        load[g] += L[i]
+    out = [np.array(sorted(g), np.int64) for g in members if g]
+    return out or [np.zeros(0, np.int64)]
 
 
-def _slice_corpus(data, offsets, a: int, b: int, symbol_bits: int):
-    """Sequences a..b-1 as their own corpus (offsets from 0; 2-bit codes repacked)."""
-    off = np.asarray(offsets, dtype=np.uint64)
-    s0, s1 = int(off[a]), int(off[b])
-    sub_off = (off[a:b + 1] - off[a]).astype(np.uint64)
+def _gather_corpus(data, offsets, idx, symbol_bits: int):
+    """Sequences `idx` as a corpus of their own (offsets from 0; 2-bit codes
+    repacked from the group's first base)."""
+    off = np.asarray(offsets, dtype=np.uint64).astype(np.int64)
+    L = off[idx + 1] - off[idx]
+    sub_off = np.zeros(len(idx) + 1, np.uint64)
+    sub_off[1:] = np.cumsum(L)
     if symbol_bits == 8:
-        return np.ascontiguousarray(data[s0:s1]), sub_off
-    g = np.arange(s0, s1, dtype=np.int64)
+        parts = [np.asarray(data[off[i]:off[i + 1]]) for i in idx]
+        return (np.concatenate(parts) if parts else np.zeros(0, np.uint8)), sub_off
+    g = np.concatenate([np.arange(off[i], off[i + 1], dtype=np.int64) for i in idx]) if len(idx) else \
+        np.zeros(0, np.int64)
     codes = (np.asarray(data)[g >> 2] >> (6 - 2 * (g & 3)).astype(np.uint8)) & 3
     pad = (-len(codes)) % 4
     codes = np.concatenate([codes, np.zeros(pad, np.uint8)]).reshape(-1, 4)
@@ -58,10 +65,11 @@ def _slice_corpus(data, offsets, a: int, b: int, symbol_bits: int):
 
 
 def _count_group(args):
-    path, a, b, j, prefixes, count_mode, symbol_bits = args
+    path, g, j, prefixes, count_mode, symbol_bits = args
     data = np.load(os.path.join(path, "data.npy"), mmap_mode="r")
     offsets = np.load(os.path.join(path, "offsets.npy"))
-    d, o = _slice_corpus(data, offsets, a, b, symbol_bits)
+    idx = np.load(os.path.join(path, f"group{g}.npy"))
+    d, o = _gather_corpus(data, offsets, idx, symbol_bits)
     return _oracle.count_pass(d, o, j, prefixes, count_mode=count_mode, symbol_bits=symbol_bits)
 
 
@@ -111,18 +119,20 @@ def intergrams(data, offsets, n: int, k: int, candidates: int, base_n: int = 3, 
     workers = workers or os.cpu_count() or 1
     data = np.ascontiguousarray(np.asarray(data, dtype=np.uint8))
     offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
-    groups = shard_bounds(offsets, workers)
+    groups = shard_groups(offsets, workers)
     b = min(base_n, n)
     tmp = tempfile.mkdtemp(prefix="ig_oracle_")
     out = []
     try:
         np.save(os.path.join(tmp, "data.npy"), data if data.size else np.zeros(1, np.uint8))
         np.save(os.path.join(tmp, "offsets.npy"), offsets)
+        for g, idx in enumerate(groups):
+            np.save(os.path.join(tmp, f"group{g}.npy"), idx)
         ctx = mp.get_context("spawn")  # never fork a process that may hold a GPU context
         with ctx.Pool(min(workers, len(groups))) as pool:
             P = None
             for j in range(b, n + 1):
-                tasks = [(tmp, a, e, j, P, count_mode, symbol_bits) for a, e in groups]
+                tasks = [(tmp, g, j, P, count_mode, symbol_bits) for g in range(len(groups))]
                 keys, counts = merge_counts(pool.map(_count_group, tasks))
                 if keys.shape[1] != j:
                     keys = np.zeros((0, j), np.uint8)

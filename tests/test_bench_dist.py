@@ -47,7 +47,7 @@ def test_aggregate_over_two_gloo_ranks():
 def test_reference_arm_prints_one_line(capsys):
     import json
     import bench
-    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-seqs", "8"]) == 0
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-mb", "1"]) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0

@@ -455,10 +455,14 @@ def test_sharded_two_bit_and_long_keys():
         assert np.array_equal(gk, ek) and np.array_equal(gc, ec)
 
 
-def test_shard_bounds_cover_every_sequence_once():
+def test_shard_groups_cover_every_sequence_once():
     S = _sharded()
     off = np.cumsum([0, 5, 0, 100, 1, 1, 7, 0, 300]).astype(np.uint64)
+    L = np.diff(off.astype(np.int64))
     for g in (1, 2, 3, 8, 20):
-        b = S.shard_bounds(off, g)
-        assert b[0][0] == 0 and b[-1][1] == len(off) - 1
-        assert all(x[1] == y[0] for x, y in zip(b, b[1:])) and all(a < e for a, e in b)
+        groups = S.shard_groups(off, g)
+        allidx = np.concatenate(groups)
+        assert sorted(allidx.tolist()) == list(range(len(L)))
+        assert len(groups) <= g
+        loads = sorted(int(L[x].sum()) for x in groups)
+        assert loads[-1] <= max(int(L.max()), loads[0] + int(L.max()))  # greedy by bytes
