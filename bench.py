@@ -46,7 +46,7 @@ def parse_args(argv=None):
     ap.add_argument("--max-len", type=int, default=None,
                     help="clamp sequence lengths (small cases for profiler captures)")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--cpu-mb", type=float, default=24.0,
+    ap.add_argument("--cpu-mb", type=float, default=48.0,
                     help="MB of the workload in the all-core oracle's timed sample")
     ap.add_argument("--cpu-single-mb", type=float, default=8.0,
                     help="MB of the workload in the single-core oracle's timed sample")

@@ -162,9 +162,15 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
  * candidate settings on a prefix of the sequences of about sample_bytes
  * (0 = 256 MiB); every candidate must return byte-identical results (else
  * IG_ESTATE). Arguments as for intergrams_plan; out receives the fastest
- * knobs, best_ms (optional) their job time on the sample. Results are cached
- * per process. intergrams_plan with IG_F_AUTOTUNE calls this for the knobs
- * left at 0. Synchronises the stream.
+ * knobs, best_ms (optional) their job time on the sample, or 0 when the
+ * knobs came from the cache without timing anything. Choices are cached per
+ * (device name and SM count, alphabet, n, base_n, candidate-count bucket,
+ * count mode, corpus-size bucket) in the process and in a text file, so a
+ * later process skips the sample runs: INTERGRAMS_TUNE_CACHE if set (empty
+ * or "none": no file), else $XDG_CACHE_HOME/intergrams/autotune.txt or
+ * $HOME/.cache/intergrams/autotune.txt (a file that cannot be read or
+ * written is ignored). intergrams_plan with IG_F_AUTOTUNE calls this for
+ * the knobs left at 0. Synchronises the stream.
  */
 ig_status intergrams_autotune(const ig_params* p, const void* data, const uint64_t* offsets, uint32_t m,
                               void* stream, uint64_t sample_bytes, ig_tuning* out, float* best_ms);

@@ -8,12 +8,25 @@
 // pass takes the tile and set size of the candidate (same CTA shape) with the
 // fastest base pass. Every candidate must return byte-identical top-k
 // rows and counts (the knobs only change speed and memory); a mismatch is
-// reported as IG_ESTATE. Choices are cached in-process per (device, alphabet,
-// n, base, candidate-count bucket, count mode, corpus-size bucket).
+// reported as IG_ESTATE. Choices are cached per (device name and SM count,
+// alphabet, n, base, candidate-count bucket, count mode, corpus-size bucket):
+// in the process, and in a cache file so that later processes skip the
+// sample runs. The file is INTERGRAMS_TUNE_CACHE if that is set (empty or
+// "none": no file), else $XDG_CACHE_HOME/intergrams/autotune.txt or
+// $HOME/.cache/intergrams/autotune.txt. One line per choice: the key, then
+// the ig_tuning fields in header order, preceded by their number (a line
+// whose field count differs from this build's is ignored). Lines are
+// appended whole; the last line for a key wins.
+#include <sys/stat.h>
+
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <sstream>
+#include <string>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -26,9 +39,83 @@ void set_last_error(const std::string& msg);
 
 namespace {
 
-using Key = std::tuple<int, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>;
+using Key = std::tuple<std::string, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>;
 std::mutex g_mu;
 std::map<Key, ig_tuning> g_cache;
+bool g_file_loaded = false;
+constexpr uint32_t kFields = sizeof(ig_tuning) / sizeof(uint32_t);
+
+std::string cache_path() {
+  const char* env = std::getenv("INTERGRAMS_TUNE_CACHE");
+  if (env) return (env[0] == 0 || std::strcmp(env, "none") == 0) ? std::string() : std::string(env);
+  std::string dir;
+  if (const char* x = std::getenv("XDG_CACHE_HOME"); x && x[0]) dir = x;
+  else if (const char* h = std::getenv("HOME"); h && h[0]) dir = std::string(h) + "/.cache";
+  else return std::string();
+  return dir + "/intergrams/autotune.txt";
+}
+
+// Device name with blanks replaced, so a key is whitespace-separated tokens.
+std::string device_token(int dev, uint32_t* sms) {
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    *sms = 0;
+    return "unknown";
+  }
+  *sms = (uint32_t)prop.multiProcessorCount;
+  std::string n = prop.name;
+  for (char& c : n)
+    if (c == ' ' || c == '\t') c = '_';
+  return n.empty() ? "unknown" : n;
+}
+
+std::string key_line(const Key& k) {
+  std::ostringstream o;
+  o << std::get<0>(k) << ' ' << std::get<1>(k) << ' ' << std::get<2>(k) << ' ' << std::get<3>(k) << ' '
+    << std::get<4>(k) << ' ' << std::get<5>(k) << ' ' << std::get<6>(k) << ' ' << std::get<7>(k);
+  return o.str();
+}
+
+// Read the cache file into g_cache (caller holds g_mu).
+void load_file_locked() {
+  g_file_loaded = true;
+  const std::string path = cache_path();
+  if (path.empty()) return;
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  char buf[1024];
+  while (std::fgets(buf, sizeof(buf), f)) {
+    std::istringstream in(buf);
+    std::string name;
+    uint32_t a[7], nf = 0;
+    if (!(in >> name >> a[0] >> a[1] >> a[2] >> a[3] >> a[4] >> a[5] >> a[6] >> nf) || nf != kFields) continue;
+    ig_tuning t{};
+    uint32_t* dst = &t.ctas_per_sm;
+    bool ok = true;
+    for (uint32_t i = 0; i < kFields && ok; ++i) ok = static_cast<bool>(in >> dst[i]);
+    if (ok) g_cache[Key{name, a[0], a[1], a[2], a[3], a[4], a[5], a[6]}] = t;
+  }
+  std::fclose(f);
+}
+
+// Append one choice to the cache file (caller holds g_mu); failures to
+// write are ignored (the file is only a cache).
+void append_file_locked(const Key& k, const ig_tuning& t) {
+  const std::string path = cache_path();
+  if (path.empty()) return;
+  for (size_t i = 1; i < path.size(); ++i)
+    if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
+  std::ostringstream o;
+  o << key_line(k) << ' ' << kFields;
+  const uint32_t* src = &t.ctas_per_sm;
+  for (uint32_t i = 0; i < kFields; ++i) o << ' ' << src[i];
+  o << '\n';
+  const std::string line = o.str();
+  FILE* f = std::fopen(path.c_str(), "a");
+  if (!f) return;
+  std::fwrite(line.data(), 1, line.size(), f);
+  std::fclose(f);
+}
 
 // knob sets tried: (ctas/SM, threads, words/thread, set log2, table load %, hot log2)
 const ig_tuning kCandidates[] = {
@@ -71,10 +158,13 @@ extern "C" ig_status intergrams_autotune(const ig_params* p, const void* data, c
   if (ms == 0) ms = std::min<uint32_t>(m, 1);
   int dev = 0;
   cudaGetDevice(&dev);
-  const Key key{dev, p->symbol_bits, p->n, p->base_n, log2_bucket(p->candidates), p->count_mode,
+  uint32_t sms = 0;
+  const std::string dname = device_token(dev, &sms);
+  const Key key{dname, sms, p->symbol_bits, p->n, p->base_n, log2_bucket(p->candidates), p->count_mode,
                 log2_bucket(h[m] + 1)};
   {
     std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_file_loaded) load_file_locked();
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
       *out = it->second;
@@ -152,6 +242,7 @@ extern "C" ig_status intergrams_autotune(const ig_params* p, const void* data, c
   {
     std::lock_guard<std::mutex> lock(g_mu);
     g_cache[key] = best_t;
+    append_file_locked(key, best_t);
   }
   *out = best_t;
   if (best_ms) *best_ms = best;

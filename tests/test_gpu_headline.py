@@ -3,7 +3,7 @@ the full malware-like workload's.
 
 The corpus follows the 8.8 GB workload's byte law (order-1 Markov bytes with
 Zipf rows, zero blocks, planted motifs) with its lognormal lengths, about
-140 MB in all, and five sequences of 4 to 8 MiB (the workload's cap). The
+230 MB in all, and five sequences of 4 to 8 MiB (the workload's cap). The
 job is the benchmark's: n = 8, k = 65,536, Z = 262,144, base 3, autotuned
 knobs. So the paths the full-size job takes - rank/select over the 67M
 candidate slots with 16-bit counters, the Eq. 2 spill lists of multi-MiB
@@ -29,7 +29,7 @@ N, K, Z, BASE = 8, 65536, 262144, 3
 LONG = [8 << 20, 7 << 20, 6 << 20, 5 << 20, 4 << 20]
 
 
-def headline_corpus(seed=21, short_bytes=110_000_000):
+def headline_corpus(seed=21, short_bytes=200_000_000):
     w = synth.WORKLOADS["malware_8gb"]
     L = synth.lengths_for(w, seed).astype(np.int64)
     L = L[np.cumsum(L) <= short_bytes]
