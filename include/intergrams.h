@@ -62,6 +62,15 @@ typedef enum {
                                       (cudaMallocAsync / cudaFreeAsync on the plan's stream) */
 #define IG_F_DRY_RUN    (1u << 6)  /* size the plan without allocating or launching anything;
                                       only intergrams_plan_device_bytes and intergrams_free apply */
+#define IG_F_SHARDED    (1u << 7)  /* this plan counts one shard of a corpus split across
+                                      processes or GPUs (intergrams_pass_scan .. _select):
+                                      32-bit counters, so every shard has the same layout */
+#define IG_F_EXHAUSTIVE_CHECKS (1u << 8) /* after every scan, check on the device that no
+                                      j-gram is counted above its (j-1)-prefix's count in the
+                                      previous pass and, for counts the plan computed itself
+                                      (not imported), that they sum to the registrations and
+                                      that no Eq. 2 count exceeds m; a failed check ends the
+                                      pass with IG_ESTATE */
 
 typedef struct {
   uint32_t n;            /* target n-gram length in symbols: 1..64 */
@@ -217,6 +226,73 @@ ig_status intergrams_rewind(ig_plan* pl);
  * a prefetch already pending), IG_ENOMEM, IG_ECUDA.
  */
 ig_status intergrams_prefetch(ig_plan* pl, const void* host_data);
+
+/* ---------------------------------------------------------------- sharding
+ * A corpus split into groups of whole sequences - across processes, or one
+ * group per GPU - is counted pass by pass as the sum of the groups' counts:
+ * sequences are independent under Eq. 1 and Eq. 2 (Sec. 2; a window never
+ * crosses a sequence boundary, and under Eq. 2 each sequence adds one per
+ * distinct n-gram). Each shard makes its plan over its own sequences with
+ * IG_F_SHARDED and the same params and layout knobs (dense_prefix, rs_depth,
+ * chain_from), then, for every pass:
+ *   intergrams_pass_scan     - the pass's corpus scan over this shard;
+ *   intergrams_counts_export - this shard's counts into a caller buffer;
+ *   (the caller sums the buffers over all shards: e.g. one all-reduce)
+ *   intergrams_counts_import - the summed counts back into the plan;
+ *   intergrams_pass_select   - the pass's selection (Algorithm 3's top-Z,
+ *                              or the top-k after pass n) on the sums.
+ * Every shard then holds the same P^(j) (the selection is deterministic), so
+ * nothing else is exchanged; intergrams_topk gives the whole corpus's rows
+ * on every shard. Calls are stream-ordered on the plan's stream; the export
+ * is complete once the stream has reached it, and the import must be
+ * enqueued after the caller's reduction has written the buffer (synchronise
+ * or order the streams). No counterpart in the paper, which runs on one
+ * machine; the partition follows from its Eq. 1/Eq. 2.
+ */
+
+/*
+ * intergrams_pass_scan - the corpus scan of the next pass, without its
+ * selection. j_out receives the pass's j. IG_DONE when every pass has run.
+ * Errors: IG_ESTATE (a scan is already pending; a plan made with IG_F_GRAPH
+ * or IG_F_DRY_RUN).
+ */
+ig_status intergrams_pass_scan(ig_plan* pl, uint32_t* j_out);
+
+/*
+ * intergrams_counts_export - the pending pass's counts into d_counts (DEVICE
+ * buffer of `capacity` uint32, stream-ordered): one count per slot of the
+ * pass, in the plan's slot order (identical on every shard). n_out receives
+ * the number of slots (also when the call fails for a small buffer).
+ * Errors: IG_ESTATE (no scan pending), IG_EINVAL (NULL, capacity < slots).
+ */
+ig_status intergrams_counts_export(ig_plan* pl, uint32_t* d_counts, uint64_t capacity, uint64_t* n_out);
+
+/*
+ * intergrams_counts_import - replace the pending pass's counts with d_counts
+ * (DEVICE, n uint32 = the pass's slots, e.g. the sum over the shards;
+ * stream-ordered). Errors: IG_ESTATE (no scan pending), IG_EINVAL (NULL, n
+ * differs from the pass's slots).
+ */
+ig_status intergrams_counts_import(ig_plan* pl, const uint32_t* d_counts, uint64_t n);
+
+/*
+ * intergrams_pass_select - the pending pass's selection on its current
+ * counts (Algorithm 3: P^(j) = top-Z, or the final top-k after pass n).
+ * j_done receives the pass's j. Synchronises once to read the device status
+ * word (errors as intergrams_pass). Errors: IG_ESTATE (no scan pending).
+ */
+ig_status intergrams_pass_select(ig_plan* pl, uint32_t* j_done);
+
+/*
+ * intergrams_shard_assign - split m sequences (HOST offsets, m + 1 entries,
+ * in symbols) into nshards groups of about equal total length, greedily by
+ * bytes: longest sequence first, each to the group with the fewest symbols
+ * so far (ties to the lower index). shard_of[i] receives sequence i's group;
+ * shard_symbols (optional, nshards entries) each group's total. Host only.
+ * Errors: IG_EINVAL (NULL, nshards == 0, decreasing offsets).
+ */
+ig_status intergrams_shard_assign(const uint64_t* offsets, uint32_t m, uint32_t nshards, uint32_t* shard_of,
+                                  uint64_t* shard_symbols);
 
 /*
  * intergrams_topk - the top-k j-grams of the latest completed pass j (paper

@@ -23,6 +23,8 @@ F_HOST_INPUT = 1 << 0
 F_GRAPH = 1 << 1
 F_AUTOTUNE = 1 << 2
 F_TIMING = 1 << 3
+F_SHARDED = 1 << 7
+F_EXHAUSTIVE_CHECKS = 1 << 8
 
 # every symbol include/intergrams.h declares
 EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_rewind", "intergrams_topk",
@@ -30,7 +32,9 @@ EXPORTS = ["intergrams_plan", "intergrams_pass", "intergrams_run", "intergrams_r
            "intergrams_dense_topk_static", "intergrams_plan_device_bytes", "intergrams_server_create",
            "intergrams_server_submit", "intergrams_server_wait", "intergrams_server_stats",
            "intergrams_server_destroy", "intergrams_autotune", "intergrams_features",
-           "intergrams_test_fail_alloc", "intergrams_test_stall_tiles", "intergrams_prefetch"]
+           "intergrams_test_fail_alloc", "intergrams_test_stall_tiles", "intergrams_prefetch",
+           "intergrams_pass_scan", "intergrams_counts_export", "intergrams_counts_import",
+           "intergrams_pass_select", "intergrams_shard_assign"]
 
 
 class IgParams(ctypes.Structure):
@@ -134,6 +138,16 @@ def load(build_if_missing: bool = True):
     lib.intergrams_prefetch.argtypes = [P, P]
     lib.intergrams_test_stall_tiles.restype = ctypes.c_int
     lib.intergrams_test_stall_tiles.argtypes = [P]
+    lib.intergrams_pass_scan.restype = ctypes.c_int
+    lib.intergrams_pass_scan.argtypes = [P, ctypes.POINTER(U32)]
+    lib.intergrams_counts_export.restype = ctypes.c_int
+    lib.intergrams_counts_export.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+    lib.intergrams_counts_import.restype = ctypes.c_int
+    lib.intergrams_counts_import.argtypes = [P, P, ctypes.c_uint64]
+    lib.intergrams_pass_select.restype = ctypes.c_int
+    lib.intergrams_pass_select.argtypes = [P, ctypes.POINTER(U32)]
+    lib.intergrams_shard_assign.restype = ctypes.c_int
+    lib.intergrams_shard_assign.argtypes = [P, U32, U32, P, P]
     _lib = lib
     return lib
 
@@ -164,11 +178,12 @@ class Plan:
     def __init__(self, data, offsets, *, n: int, k: int, candidates: int, base_n: int = 3,
                  symbol_bits: int = 8, count_mode: int = COUNT_ONCE_PER_SEQUENCE, graph: bool = False,
                  host_input: bool = False, timing: bool = False, autotune: bool = False, stream=None,
-                 tuning: dict | None = None):
+                 tuning: dict | None = None, sharded: bool = False, checks: bool = False):
         self._lib = load()
         self._h = ctypes.c_void_p(None)
         flags = ((F_GRAPH if graph else 0) | (F_HOST_INPUT if host_input else 0) | (F_TIMING if timing else 0)
-                 | (F_AUTOTUNE if autotune else 0))
+                 | (F_AUTOTUNE if autotune else 0) | (F_SHARDED if sharded else 0)
+                 | (F_EXHAUSTIVE_CHECKS if checks else 0))
         self.params = IgParams(n, k, candidates, base_n, symbol_bits, count_mode, flags)
         tun = IgTuning(**(tuning or {}))
         if host_input:
@@ -265,6 +280,36 @@ class Plan:
         r = npass.value
         return scan[:r].copy(), pas[:r].copy(), kern.value
 
+    # sharded passes (include/intergrams.h): scan, export, (caller sums), import, select
+    def pass_scan(self):
+        """Scan of the next pass only; its j, or None when every pass has run."""
+        j = ctypes.c_uint32(0)
+        st = _check(self._lib, self._lib.intergrams_pass_scan(self._h, ctypes.byref(j)), "intergrams_pass_scan")
+        return None if st == IG_DONE else j.value
+
+    def counts_export(self, out):
+        """The pending pass's counts into ``out`` (a CUDA uint32/int32 tensor
+        with room for them); returns the number of slots."""
+        n = ctypes.c_uint64(0)
+        _check(self._lib, self._lib.intergrams_counts_export(self._h, _ptr(out), out.numel(), ctypes.byref(n)),
+               "intergrams_counts_export")
+        return n.value
+
+    def counts_slots(self):
+        """Number of counters of the pending pass."""
+        n = ctypes.c_uint64(0)
+        self._lib.intergrams_counts_export(self._h, None, 0, ctypes.byref(n))
+        return n.value
+
+    def counts_import(self, counts):
+        _check(self._lib, self._lib.intergrams_counts_import(self._h, _ptr(counts), counts.numel()),
+               "intergrams_counts_import")
+
+    def pass_select(self):
+        j = ctypes.c_uint32(0)
+        _check(self._lib, self._lib.intergrams_pass_select(self._h, ctypes.byref(j)), "intergrams_pass_select")
+        return j.value
+
     def test_stall_tiles(self):
         """Test hook: later corpus scans wait for tiles that are never sent,
         so their passes raise IG_ETIMEOUT after about a second."""
@@ -321,6 +366,19 @@ def dense_topk_static(data, offsets, *, n: int, k: int, symbol_bits: int = 8,
                                           stream_ptr, _ptr(keys_out), _ptr(counts_out), _ptr(rows_out),
                                           _ptr(status_out))
     _check(lib, st, "intergrams_dense_topk_static")
+
+
+def shard_assign(offsets, nshards: int):
+    """Byte-balanced greedy split of the sequences (intergrams_shard_assign):
+    (shard of each sequence uint32[m], symbols per shard uint64[nshards])."""
+    lib = load(build_if_missing=False) if _build.LIB.joinpath("libintergrams.so").exists() else load()
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    m = len(off) - 1
+    out = np.zeros(max(m, 1), np.uint32)
+    loads = np.zeros(max(nshards, 1), np.uint64)
+    _check(lib, lib.intergrams_shard_assign(off.ctypes.data, m, nshards, out.ctypes.data, loads.ctypes.data),
+           "intergrams_shard_assign")
+    return out[:m].copy(), loads[:nshards].copy()
 
 
 def test_stall_next_static_call():

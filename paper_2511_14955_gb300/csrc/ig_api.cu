@@ -171,6 +171,12 @@ struct ig_plan {
   cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
   bool check_overflow = false;
   bool narrow = false;               // 16-bit counters (every count provably < 65536)
+  uint32_t pending_j = 0;            // sharded pass: scan of pass pending_j done, selection not yet
+  bool imported = false;             // the pending pass's counts were replaced by intergrams_counts_import
+  // IG_F_EXHAUSTIVE_CHECKS: the previous pass's selected counts by counter
+  // row of this pass, and the sum of this pass's counters
+  uint32_t* prev_count = nullptr;
+  unsigned long long* check_sum = nullptr;
   // registration log of the candidate passes (counter arrays far larger than L2)
   uint32_t* rlog = nullptr;
   uint32_t* rlog_range = nullptr;
@@ -241,7 +247,7 @@ void release(ig_plan* pl) {
                   pl->sel_hist, pl->sel_count, pl->d_tile_base, pl->lists[0], pl->lists[1], pl->list_off[0],
                   pl->list_off[1], pl->list_cnt[0], pl->list_cnt[1], pl->hist, pl->blk, pl->sidx[0], pl->sidx[1], pl->skey[0],
                   pl->skey[1], pl->shist, pl->spill, pl->ctl, pl->d_order, pl->out_keys, pl->out_counts,
-                  pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank,
+                  pl->alive[0], pl->alive[1], pl->hot, pl->hot_pick, pl->rank, pl->prev_count, pl->check_sum,
                   pl->rlog, pl->rlog_range, pl->rlog_fill, pl->bitmap, pl->dmap, pl->rs[0], pl->rs[1], pl->rs[2], pl->rs[3], pl->rs_sums, pl->feat_keys,
                   pl->feat_table, pl->feat_q, pl->feat_nnz, pl->feat_rowptr};
   for (void* q : ptrs) device_free(q, pl->async_alloc, pl->stream);
@@ -281,8 +287,57 @@ bool rs_pass(const ig_plan* pl, uint32_t j) {
 // Kernels of one sort by count: init + (histogram, two scans, scatter) per 8-bit digit.
 uint32_t sort_kernels(const ig_plan* pl) { return 1 + 4 * (pl->narrow ? 2u : 4u); }
 
-// Enqueue pass j (no host synchronisation); returns the kernels launched.
-uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
+// IG_F_EXHAUSTIVE_CHECKS. Every counter of the pass: the sum over all of
+// them (must equal the registrations: each one increments one counter by
+// one), Eq. 2 counts at most `limit` = m, and - with the previous pass's
+// counts by row - no j-gram above its (j-1)-prefix (a window of the j-gram
+// is a window of the prefix; the prefix's count was exact).
+__global__ void check_counts_kernel(const uint32_t* counts, bool narrow, uint64_t ns, uint32_t row_shift,
+                                    const uint32_t* prev_count, uint32_t limit, unsigned long long* sum,
+                                    PassCtl* ctl) {
+  unsigned long long local = 0;
+  bool bad = false;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < ns; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = narrow ? (counts[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu : counts[i];
+    local += c;
+    if (c > limit) bad = true;
+    if (prev_count && c > prev_count[i >> row_shift]) bad = true;
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31u) == 0 && local) atomicAdd(sum, local);
+  if (bad) atomicOr(&ctl->status, kStCheck);
+}
+
+__global__ void check_sum_kernel(const unsigned long long* sum, PassCtl* ctl) {
+  if (threadIdx.x == 0 && *sum != ctl->registrations) atomicOr(&ctl->status, kStCheck);
+}
+
+// The selected counts by the next pass's counter row: byte-order id (a
+// rank/select pass) or rank by count.
+__global__ void prev_count_kernel(const uint32_t* sel_count, const uint32_t* rank, const PassCtl* ctl,
+                                  uint32_t* prev_count) {
+  const uint32_t n = ctl->nsel;
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+    prev_count[rank ? rank[x] : x] = sel_count[x];
+}
+
+// Counters of pass j: narrow (16-bit) <-> the 32-bit exchange format.
+__global__ void widen_counts_kernel(const uint32_t* packed, uint64_t ns, uint32_t* out) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < ns; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (packed[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu;
+}
+__global__ void narrow_counts_kernel(const uint32_t* in, uint64_t ns, uint32_t* packed, PassCtl* ctl) {
+  const uint64_t words = (ns + 1) / 2;
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t lo = in[2 * w], hi = 2 * w + 1 < ns ? in[2 * w + 1] : 0u;
+    if ((lo | hi) > 0xFFFFu) atomicOr(&ctl->status, kStCountOverflow);
+    packed[w] = (lo & 0xFFFFu) | (hi << 16);
+  }
+}
+
+// Enqueue the scan half of pass j (reset, counters cleared, corpus scan);
+// returns the kernels launched.
+uint32_t enqueue_scan(ig_plan* pl, uint32_t j, cudaStream_t s) {
   const uint32_t md = mode_of(pl, j), md_next = mode_of(pl, j + 1);
   const bool base = (md == kModeBase);
   const bool timing = (pl->p.flags & IG_F_TIMING) != 0;
@@ -391,6 +446,37 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
     }
   }
   if (timing) cudaEventRecordWithFlags(pl->ev_scan1[ti], s, evf);
+  return kernels;
+}
+
+// Enqueue the selection half of pass j (its top-T and, before pass j + 1,
+// the candidate set P^(j)) on the counts the scan left; returns the kernels
+// launched.
+uint32_t enqueue_select(ig_plan* pl, uint32_t j, cudaStream_t s) {
+  const uint32_t md = mode_of(pl, j), md_next = mode_of(pl, j + 1);
+  const bool base = (md == kModeBase);
+  const bool timing = (pl->p.flags & IG_F_TIMING) != 0;
+  const uint32_t ti = j - pl->b;
+  const uint64_t ns = base ? pl->nslots_base : pl->nslots_cand;
+  uint32_t* sel = pl->sel_hist + (uint64_t)(j - pl->b) * pl->p.candidates;
+  uint32_t kernels = 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (timing) cudaStreamIsCapturing(s, &cs);
+  const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (pl->check_sum) {
+    cudaMemsetAsync(pl->check_sum, 0, sizeof(unsigned long long), s);
+    // counts imported from a sum over shards may reach the whole corpus's m:
+    // only the prefix check applies to them
+    const uint32_t limit =
+        (pl->p.count_mode == IG_COUNT_ONCE_PER_SEQUENCE && !pl->imported) ? pl->m : 0xFFFFFFFFu;
+    check_counts_kernel<<<4 * 152, 256, 0, s>>>(pl->counts, pl->narrow, ns, pl->sb, base ? nullptr : pl->prev_count,
+                                                limit, pl->check_sum, pl->ctl);
+    kernels += 1;
+    if (!pl->imported) {
+      check_sum_kernel<<<1, 32, 0, s>>>(pl->check_sum, pl->ctl);
+      kernels += 1;
+    }
+  }
   const uint32_t target = (j < pl->p.n) ? pl->p.candidates : pl->p.k;
   // the scan of a candidate pass counted in rank space; selection reads the
   // counters back in byte order through the rank map
@@ -425,10 +511,23 @@ uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
       launch_build_hot(pl->keys[nxt], pl->sel_count, pl->rank, pl->ctl, pl->hot, pl->hot_pick, pl->hot_log2, s);
       kernels += 3;
     }
+    if (pl->prev_count) {  // rows without a candidate keep 0: any count there fails the check
+      cudaMemsetAsync(pl->prev_count, 0, sizeof(uint32_t) * pl->p.candidates, s);
+      prev_count_kernel<<<256, 256, 0, s>>>(pl->sel_count, rs_pass(pl, j + 1) ? nullptr : pl->rank, pl->ctl,
+                                            pl->prev_count);
+      kernels += 1;
+    }
   }
   if (timing) cudaEventRecordWithFlags(pl->ev_pass1[ti], s, evf);
   return kernels;
 }
+
+// Enqueue pass j (no host synchronisation); returns the kernels launched.
+uint32_t enqueue_pass(ig_plan* pl, uint32_t j, cudaStream_t s) {
+  const uint32_t k = enqueue_scan(pl, j, s);
+  return k + enqueue_select(pl, j, s);
+}
+
 
 // After pass j has been enqueued: bookkeeping on the host.
 void finish_pass_host(ig_plan* pl, uint32_t j) {
@@ -447,6 +546,9 @@ ig_status read_status(ig_plan* pl) {
   if (st & kStListFull) return fail(IG_ETABLE_FULL, "a survivor list exceeded its capacity (raise list_pct)");
   if (st & kStTimeout) return fail(IG_ETIMEOUT, "a tile's bulk copy did not complete");
   if (st & (kStSetFull | kStTableFull)) return fail(IG_ETABLE_FULL, "a device hash table filled up");
+  if (st & kStCheck)
+    return fail(IG_ESTATE, "an exhaustive check failed: counters do not sum to the registrations, an Eq. 2 count "
+                           "exceeds m, or a j-gram's count exceeds its prefix's");
   if (st) return fail(IG_ECUDA, "device status error");
   return IG_OK;
 }
@@ -481,6 +583,9 @@ ig_status plan_last_status(ig_plan* pl) {
   if (st & kStListFull) return fail(IG_ETABLE_FULL, "a survivor list exceeded its capacity (raise list_pct)");
   if (st & kStTimeout) return fail(IG_ETIMEOUT, "a tile's bulk copy did not complete");
   if (st & (kStSetFull | kStTableFull)) return fail(IG_ETABLE_FULL, "a device hash table filled up");
+  if (st & kStCheck)
+    return fail(IG_ESTATE, "an exhaustive check failed: counters do not sum to the registrations, an Eq. 2 count "
+                           "exceeds m, or a j-gram's count exceeds its prefix's");
   if (st) return fail(IG_ECUDA, "device status error");
   return IG_OK;
 }
@@ -647,6 +752,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   // Eq. 1 counts at most the number of windows (halves the counter array, so
   // far more of it stays in L2)
   pl->narrow = (p->count_mode == IG_COUNT_ONCE_PER_SEQUENCE) ? (m < 65536u) : (pl->total_syms < 65536u);
+  if (p->flags & IG_F_SHARDED) pl->narrow = false;  // shards agree on one counter layout
 
   // scan launch geometry: shared memory = dedupe set + hot cache + tile (with
   // halo and alignment slop) + candidate queue (2 bytes per tile window) +
@@ -744,6 +850,10 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   PLAN_CUDA(dev_alloc(pl, &pl->sel_hist, (size_t)(p->n - pl->b + 1) * p->candidates));
   PLAN_CUDA(dev_alloc(pl, &pl->sel_count, p->candidates));
   PLAN_CUDA(dev_alloc(pl, &pl->rank, p->candidates));
+  if (p->flags & IG_F_EXHAUSTIVE_CHECKS) {
+    PLAN_CUDA(dev_alloc(pl, &pl->prev_count, p->candidates));
+    PLAN_CUDA(dev_alloc(pl, &pl->check_sum, 1));
+  }
   PLAN_CUDA(dev_alloc(pl, &pl->hist, (size_t)kMaxLevels * kHistBins));
   PLAN_CUDA(dev_alloc(pl, &pl->blk, (size_t)2 * pl->G));
   PLAN_CUDA(dev_alloc(pl, &pl->sidx[0], pl->sort_cap));
@@ -885,6 +995,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
 ig_status intergrams_pass(ig_plan* pl, uint32_t* j_done) {
   g_last_error.clear();
   if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  if (pl->pending_j) return fail(IG_ESTATE, "a sharded pass is waiting for intergrams_pass_select");
   if (pl->next_j > pl->p.n) return IG_DONE;
   const uint32_t j = pl->next_j;
   char name[32];
@@ -901,6 +1012,7 @@ ig_status intergrams_run(ig_plan* pl) {
   g_last_error.clear();
   if (!pl) return fail(IG_EINVAL, "plan is NULL");
   Range range("ig run");
+  if (pl->pending_j) return fail(IG_ESTATE, "a sharded pass is waiting for intergrams_pass_select");
   if (pl->next_j > pl->p.n) return IG_OK;
   const bool from_start = pl->next_j == pl->b;
   if ((pl->p.flags & IG_F_GRAPH) && from_start) {
@@ -943,6 +1055,7 @@ ig_status intergrams_rewind(ig_plan* pl) {
   if (!pl) return fail(IG_EINVAL, "plan is NULL");
   pl->cur = 0;  // the key buffers' parity at the start of a run (graphs are captured with it)
   pl->next_j = pl->b;
+  pl->pending_j = 0;
   pl->last_j = 0;
   pl->nsel_last = 0;
   pl->kernels = 0;
@@ -984,6 +1097,110 @@ ig_status intergrams_prefetch(ig_plan* pl, const void* host_data) {
   IG_CUDA(cudaMemcpyAsync(dst, host_data, pl->data_bytes, cudaMemcpyHostToDevice, pl->copy_stream));
   IG_CUDA(cudaEventRecord(pl->ev_copied, pl->copy_stream));
   pl->prefetched = true;
+  return IG_OK;
+}
+
+// ---- sharded passes --------------------------------------------------------
+
+ig_status intergrams_pass_scan(ig_plan* pl, uint32_t* j_out) {
+  g_last_error.clear();
+  if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  if (pl->dry_run) return fail(IG_ESTATE, "dry-run plan");
+  if (pl->p.flags & IG_F_GRAPH) return fail(IG_ESTATE, "sharded passes are launched one by one (no IG_F_GRAPH)");
+  if (pl->pending_j) return fail(IG_ESTATE, "the previous scan is waiting for intergrams_pass_select");
+  if (pl->next_j > pl->p.n) return IG_DONE;
+  const uint32_t j = pl->next_j;
+  char name[40];
+  std::snprintf(name, sizeof(name), "ig pass %u scan", j);
+  Range range(name);
+  pl->kernels += enqueue_scan(pl, j, pl->stream);
+  IG_CUDA(cudaGetLastError());
+  pl->pending_j = j;
+  pl->imported = false;
+  if (j_out) *j_out = j;
+  return IG_OK;
+}
+
+// Slots of the pending pass's counters.
+static uint64_t pending_slots(const ig_plan* pl) {
+  return mode_of(pl, pl->pending_j) == kModeBase ? pl->nslots_base : pl->nslots_cand;
+}
+
+ig_status intergrams_counts_export(ig_plan* pl, uint32_t* d_counts, uint64_t capacity, uint64_t* n_out) {
+  g_last_error.clear();
+  if (!pl || !n_out) return fail(IG_EINVAL, "plan or n_out is NULL");
+  if (!pl->pending_j) return fail(IG_ESTATE, "no scan is pending (call intergrams_pass_scan first)");
+  const uint64_t ns = pending_slots(pl);
+  *n_out = ns;
+  if (!d_counts || capacity < ns) return fail(IG_EINVAL, "counts buffer is NULL or smaller than the pass's slots");
+  if (pl->narrow) {
+    widen_counts_kernel<<<4 * 152, 256, 0, pl->stream>>>(pl->counts, ns, d_counts);
+    pl->kernels += 1;
+  } else {
+    IG_CUDA(cudaMemcpyAsync(d_counts, pl->counts, ns * sizeof(uint32_t), cudaMemcpyDeviceToDevice, pl->stream));
+  }
+  IG_CUDA(cudaGetLastError());
+  return IG_OK;
+}
+
+ig_status intergrams_counts_import(ig_plan* pl, const uint32_t* d_counts, uint64_t n) {
+  g_last_error.clear();
+  if (!pl || !d_counts) return fail(IG_EINVAL, "plan or counts is NULL");
+  if (!pl->pending_j) return fail(IG_ESTATE, "no scan is pending (call intergrams_pass_scan first)");
+  const uint64_t ns = pending_slots(pl);
+  if (n != ns) return fail(IG_EINVAL, "count array length differs from the pass's slots");
+  if (pl->narrow) {
+    narrow_counts_kernel<<<4 * 152, 256, 0, pl->stream>>>(d_counts, ns, pl->counts, pl->ctl);
+    pl->kernels += 1;
+  } else {
+    IG_CUDA(cudaMemcpyAsync(pl->counts, d_counts, ns * sizeof(uint32_t), cudaMemcpyDeviceToDevice, pl->stream));
+  }
+  IG_CUDA(cudaGetLastError());
+  pl->imported = true;
+  return IG_OK;
+}
+
+ig_status intergrams_pass_select(ig_plan* pl, uint32_t* j_done) {
+  g_last_error.clear();
+  if (!pl) return fail(IG_EINVAL, "plan is NULL");
+  if (!pl->pending_j) return fail(IG_ESTATE, "no scan is pending (call intergrams_pass_scan first)");
+  const uint32_t j = pl->pending_j;
+  char name[40];
+  std::snprintf(name, sizeof(name), "ig pass %u select", j);
+  Range range(name);
+  pl->kernels += enqueue_select(pl, j, pl->stream);
+  IG_CUDA(cudaGetLastError());
+  pl->pending_j = 0;
+  pl->imported = false;
+  finish_pass_host(pl, j);
+  if (j_done) *j_done = j;
+  return read_status(pl);
+}
+
+ig_status intergrams_shard_assign(const uint64_t* offsets, uint32_t m, uint32_t nshards, uint32_t* shard_of,
+                                  uint64_t* shard_symbols) {
+  g_last_error.clear();
+  if (!offsets || (m && !shard_of) || nshards == 0) return fail(IG_EINVAL, "NULL argument or no shards");
+  std::vector<uint32_t> order(m);
+  for (uint32_t i = 0; i < m; ++i) {
+    if (offsets[i + 1] < offsets[i]) return fail(IG_EINVAL, "offsets decrease");
+    order[i] = i;
+  }
+  // longest sequence first (ties: lower index first), each to the shard
+  // with the fewest symbols so far (ties: lower shard)
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+  });
+  std::vector<uint64_t> load(nshards, 0);
+  for (uint32_t i : order) {
+    uint32_t best = 0;
+    for (uint32_t g = 1; g < nshards; ++g)
+      if (load[g] < load[best]) best = g;
+    shard_of[i] = best;
+    load[best] += offsets[i + 1] - offsets[i];
+  }
+  if (shard_symbols)
+    for (uint32_t g = 0; g < nshards; ++g) shard_symbols[g] = load[g];
   return IG_OK;
 }
 

@@ -34,6 +34,7 @@ enum : uint32_t {
   kStQueue = 1u << 3,          // work queue inconsistency
   kStListFull = 1u << 4,       // a survivor list ran out of its capacity
   kStTimeout = 1u << 5,        // a bounded wait for a tile's bulk copy ran out
+  kStCheck = 1u << 6,          // an exhaustive check failed (IG_F_EXHAUSTIVE_CHECKS)
 };
 
 // Device-side control block, one per plan. The pass fields are zeroed at the
