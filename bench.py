@@ -52,8 +52,11 @@ def parse_args(argv=None):
                     help="MB of the workload in the single-core oracle's timed sample")
     ap.add_argument("--ref-mb", type=float, default=6.0, help="MB of the workload per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=120, help="jobs in the serving leg (0 = skip)")
+    ap.add_argument("--serve-jobs", type=int, default=2000, help="jobs in the serving leg (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-jobs-4x", type=int, default=400, help="jobs of the four-times-rate stream")
+    ap.add_argument("--serve-corpora", type=int, default=96, help="device-resident corpora the jobs draw from")
+    ap.add_argument("--serve-max-gb", type=float, default=2.0, help="largest job corpus (GiB)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--count-mode", type=int, choices=[0, 1], default=0,
                     help="0 = once per sequence (Eq. 2, the headline), 1 = every occurrence (Eq. 1)")
@@ -284,24 +287,30 @@ def recall_leg(seed: int):
 
 
 def serving_leg(args, seed):
-    """Poisson job stream (20 jobs/s; corpora of the 2 MiB workload's byte law,
-    total sizes lognormal with median 64 MB, clamped to [1 MB, 512 MB] here to
-    bound the run; n in {4, 8, 16}; k in {1K, 16K, 256K}; Z = 4k) through the
-    continuous-batching server, and the same stream one job per launch."""
+    """Poisson job stream (config 5: jobs at 20/s over corpora of the 2 MiB
+    workload's byte law, total sizes lognormal with median 64 MB, clamped to
+    [1 MB, 2 GB]; n in {4, 8, 16}; k in {1K, 16K, 256K}; Z = 4k) through the
+    continuous-batching server (least work first, stream priorities by work),
+    and the same stream one job per launch in arrival order. Each job takes a
+    corpus from a pool of device-resident corpora drawn from the size law.
+    The same job mix at four times the rate is a second, shorter stream."""
+    import numpy as np
     from paper_2511_14955_gb300 import serving
-    pool = serving.make_pool(8, seed=seed + 7, hi_bytes=512 << 20)
+    pool = serving.make_pool(args.serve_corpora, seed=seed + 7, hi_bytes=int(args.serve_max_gb * (1 << 30)))
     jobs = serving.job_stream(args.serve_jobs, args.serve_rate, len(pool), seed=seed + 11)
     tun = {"list_pct": 50}
     batched = serving.run_stream(pool, jobs, max_active=8, tuning=tun)
-    single = serving.run_stream(pool, jobs, max_active=1, tuning=tun)
+    single = serving.run_stream(pool, jobs, max_active=1, tuning=tun, fifo=True)
+    sizes = np.array([int(o[-1]) for _, o in pool])
     out = {"workload": f"{len(jobs)} Poisson jobs at {args.serve_rate:g}/s over {len(pool)} corpora "
-                       f"({sum(int(o[-1]) for _, o in pool) / 1e6:.0f} MB), n in {{4,8,16}}, k in {{1K,16K,256K}}",
+                       f"({sizes.sum() / 1e9:.1f} GB; sizes {sizes.min() / 1e6:.1f} MB .. {sizes.max() / 1e9:.2f} GB, "
+                       f"median {np.median(sizes) / 1e6:.0f} MB), n in {{4,8,16}}, k in {{1K,16K,256K}}, Z = 4k",
            "continuous_batching": batched, "one_job_per_launch": single}
-    # the same job mix at four times the arrival rate, where jobs overlap
-    hot = serving.job_stream(args.serve_jobs, 4 * args.serve_rate, len(pool), seed=seed + 11)
-    out["at_4x_rate"] = {"rate_per_s": 4 * args.serve_rate,
+    hot = serving.job_stream(args.serve_jobs_4x, 4 * args.serve_rate, len(pool), seed=seed + 11)
+    out["at_4x_rate"] = {"rate_per_s": 4 * args.serve_rate, "jobs": len(hot),
                          "continuous_batching": serving.run_stream(pool, hot, max_active=8, tuning=tun),
-                         "one_job_per_launch": serving.run_stream(pool, hot, max_active=1, tuning=tun)}
+                         "one_job_per_launch": serving.run_stream(pool, hot, max_active=1, tuning=tun, fifo=True)}
+    del pool
     return out
 
 

@@ -427,8 +427,19 @@ typedef struct ig_server ig_server;
 typedef struct {
   uint64_t mem_budget;   /* device bytes all active jobs' tables may use (0 = 80% of free memory) */
   uint32_t max_active;   /* jobs in flight at once (0 = 8) */
-  uint32_t flags;        /* reserved, 0 */
+  uint32_t flags;        /* IG_SRV_* */
 } ig_server_config;
+/* Server policy flags. Default (0): admit the pending job with the least
+ * estimated work first (corpus bytes x passes plus its counter arrays; the
+ * estimate halves for every 100 ms a job has waited, so none starves), on a
+ * CUDA stream whose priority falls with the job's work (three classes:
+ * below 1 GB, below 8 GB, more), so a small job's pass is started before a
+ * large job's next pass. IG_SRV_FIFO: arrival order, default priority. */
+#define IG_SRV_FIFO (1u << 0)
+/* IG_SRV_OLDEST_FIRST: arrival order, and each job's stream one priority
+ * level below the jobs already running when it was admitted, so the oldest
+ * job's passes start first and younger jobs fill the gaps it leaves. */
+#define IG_SRV_OLDEST_FIRST (1u << 1)
 typedef struct {
   uint64_t submitted, completed, failed;
   uint32_t active, peak_active, pending;

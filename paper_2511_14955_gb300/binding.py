@@ -24,6 +24,8 @@ F_GRAPH = 1 << 1
 F_AUTOTUNE = 1 << 2
 F_TIMING = 1 << 3
 F_SHARDED = 1 << 7
+SRV_FIFO = 1 << 0
+SRV_OLDEST_FIRST = 1 << 1
 F_EXHAUSTIVE_CHECKS = 1 << 8
 
 # every symbol include/intergrams.h declares
@@ -393,10 +395,13 @@ class Server:
     """Continuous-batching job server (intergrams_server_*): submit jobs whose
     corpora are CUDA tensors, wait for their top-k. Marshalling only."""
 
-    def __init__(self, mem_budget: int = 0, max_active: int = 8):
+    def __init__(self, mem_budget: int = 0, max_active: int = 8, fifo: bool = False, policy: str | None = None):
+        """policy: "least_work_first" (default), "oldest_first" or "fifo"."""
         self._lib = load()
         self._h = ctypes.c_void_p(None)
-        cfg = IgServerConfig(int(mem_budget), int(max_active), 0)
+        policy = policy or ("fifo" if fifo else "least_work_first")
+        flags = {"least_work_first": 0, "oldest_first": SRV_OLDEST_FIRST, "fifo": SRV_FIFO}[policy]
+        cfg = IgServerConfig(int(mem_budget), int(max_active), flags)
         _check(self._lib, self._lib.intergrams_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "intergrams_server_create")
         self._keep = {}

@@ -1,10 +1,16 @@
 // Serving engine: continuous batching of top-k n-gram jobs on one GPU.
 //
 // Callers submit jobs (a corpus already on the device, host offsets, the
-// job's parameters). A scheduler thread admits pending jobs in arrival order
-// whenever a slot is free and the job's tables fit the device-memory budget
-// (sizes come from a dry-run plan), gives each admitted job its own plan and
-// stream, and then advances every active job one pass at a time: whenever a
+// job's parameters). A scheduler thread admits pending jobs whenever a slot
+// is free and the job's tables fit the device-memory budget (sizes come from
+// a dry-run plan) - by default the job with the least estimated work first
+// (corpus bytes times passes, plus its counter arrays), with the wait counted
+// in so that no job starves, and on a stream whose priority falls with the
+// job's work, so that at every kernel boundary the GPU's block scheduler
+// starts a small job's pass before a large job's next one; with
+// IG_SRV_FIFO in arrival order on default-priority streams. It gives each
+// admitted job its own plan and stream, and then advances every active job
+// one pass at a time: whenever a
 // job's previous step has completed on the GPU it enqueues the job's next
 // pass (or its final top-k). Jobs at different passes therefore have work in
 // flight on the device at the same time, each job's candidate and count
@@ -52,6 +58,8 @@ struct Job {
   std::vector<uint64_t> offsets;
   uint32_t m = 0;
   uint64_t bytes = 0;  // device bytes charged against the budget
+  double work = 0;     // estimated work: bytes streamed over all passes
+  uint32_t behind = 0; // jobs already running when it was admitted
   ig_plan* plan = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
@@ -72,6 +80,10 @@ struct Job {
 struct ig_server {
   ig_server_config cfg{};
   int device = 0;
+  // pinned host buffers for results, kept for reuse (pinning is slow and
+  // freeing pinned memory can synchronise the device): size -> buffers
+  std::multimap<size_t, void*> pinned_free;
+  std::mutex pinned_mu;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Job*> pending;
@@ -85,30 +97,59 @@ struct ig_server {
 
 namespace {
 
-void release_job_resources(Job* jb) {
+// A pinned buffer of at least `bytes` (sizes rounded up to powers of two).
+void* pinned_take(ig_server* sv, size_t bytes) {
+  size_t sz = 4096;
+  while (sz < bytes) sz <<= 1;
+  {
+    std::lock_guard<std::mutex> lock(sv->pinned_mu);
+    auto it = sv->pinned_free.find(sz);
+    if (it != sv->pinned_free.end()) {
+      void* p = it->second;
+      sv->pinned_free.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, sz) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void pinned_give(ig_server* sv, void* p, size_t bytes) {
+  if (!p) return;
+  size_t sz = 4096;
+  while (sz < bytes) sz <<= 1;
+  std::lock_guard<std::mutex> lock(sv->pinned_mu);
+  sv->pinned_free.emplace(sz, p);
+}
+
+size_t keys_bytes(const Job* jb) { return std::max<size_t>((size_t)jb->p.k * jb->row_bytes, 1); }
+
+void release_job_resources(ig_server* sv, Job* jb) {
   if (jb->plan) intergrams_free(jb->plan);  // synchronises the job's stream
   jb->plan = nullptr;
   if (jb->ev) cudaEventDestroy(jb->ev);
   jb->ev = nullptr;
   if (jb->stream) cudaStreamDestroy(jb->stream);
   jb->stream = nullptr;
-  if (jb->keys_pinned) cudaFreeHost(jb->keys_pinned);
+  pinned_give(sv, jb->keys_pinned, keys_bytes(jb));
   jb->keys_pinned = nullptr;
-  if (jb->counts_pinned) cudaFreeHost(jb->counts_pinned);
+  pinned_give(sv, jb->counts_pinned, sizeof(uint64_t) * jb->p.k);
   jb->counts_pinned = nullptr;
 }
 
 void finish_job(ig_server* sv, Job* jb, ig_status st, const std::string& err) {
+  const Clock::time_point done = Clock::now();  // the job's last GPU step has completed
   if (st == IG_OK && jb->rows) {
     jb->keys.assign(jb->keys_pinned, jb->keys_pinned + (size_t)jb->rows * jb->row_bytes);
     jb->counts.assign(jb->counts_pinned, jb->counts_pinned + jb->rows);
   }
-  release_job_resources(jb);
+  release_job_resources(sv, jb);
   std::lock_guard<std::mutex> lock(sv->mu);
   jb->status = st;
   jb->err = err;
   jb->state = kDone;
-  jb->t_done = Clock::now();
+  jb->t_done = done;
   sv->mem_used -= jb->bytes;
   sv->active -= 1;
   if (st == IG_OK) sv->completed += 1;
@@ -117,9 +158,24 @@ void finish_job(ig_server* sv, Job* jb, ig_status st, const std::string& err) {
   sv->cv_work.notify_all();
 }
 
+// Work classes for stream priorities: below 1 GB, below 8 GB of bytes
+// streamed, and the rest.
+int stream_priority(const ig_server* sv, const Job* jb) {
+  if (sv->cfg.flags & IG_SRV_FIFO) return 0;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+  if (sv->cfg.flags & IG_SRV_OLDEST_FIRST) {
+    // admitted behind `active - 1` older jobs: one level below each
+    return std::min(least, greatest + (int)jb->behind);
+  }
+  if (jb->work < 1e9) return greatest;
+  if (jb->work < 8e9) return (least + greatest) / 2;
+  return least;
+}
+
 // Create the job's plan, stream and result buffers (scheduler thread).
-ig_status admit_job(Job* jb, std::string* err) {
-  if (cudaStreamCreateWithFlags(&jb->stream, cudaStreamNonBlocking) != cudaSuccess ||
+ig_status admit_job(ig_server* sv, Job* jb, std::string* err) {
+  if (cudaStreamCreateWithPriority(&jb->stream, cudaStreamNonBlocking, stream_priority(sv, jb)) != cudaSuccess ||
       cudaEventCreateWithFlags(&jb->ev, cudaEventDisableTiming) != cudaSuccess) {
     *err = "stream/event creation failed";
     return IG_ECUDA;
@@ -133,9 +189,9 @@ ig_status admit_job(Job* jb, std::string* err) {
     return st;
   }
   jb->row_bytes = ig::plan_row_bytes(jb->plan);
-  const size_t kb = std::max<size_t>((size_t)jb->p.k * jb->row_bytes, 1);
-  if (cudaMallocHost(reinterpret_cast<void**>(&jb->keys_pinned), kb) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&jb->counts_pinned), sizeof(uint64_t) * jb->p.k) != cudaSuccess) {
+  jb->keys_pinned = static_cast<uint8_t*>(pinned_take(sv, keys_bytes(jb)));
+  jb->counts_pinned = static_cast<uint64_t*>(pinned_take(sv, sizeof(uint64_t) * jb->p.k));
+  if (!jb->keys_pinned || !jb->counts_pinned) {
     *err = "pinned host allocation failed";
     return IG_ENOMEM;
   }
@@ -150,13 +206,29 @@ void scheduler(ig_server* sv) {
     {
       std::unique_lock<std::mutex> lock(sv->mu);
       if (sv->stop && sv->pending.empty() && running.empty()) break;
-      // admission: arrival order, while a slot is free and the budget allows
+      // admission while a slot is free and the budget allows: arrival order
+      // (IG_SRV_FIFO), else the least work first, each job's work discounted
+      // by its wait (it halves for every 100 ms waited, so none starves)
       while (!sv->pending.empty() && sv->active < sv->cfg.max_active) {
-        Job* jb = sv->pending.front();
+        auto pick = sv->pending.begin();
+        if (!(sv->cfg.flags & (IG_SRV_FIFO | IG_SRV_OLDEST_FIRST))) {
+          const Clock::time_point now = Clock::now();
+          double best = 0;
+          for (auto it = sv->pending.begin(); it != sv->pending.end(); ++it) {
+            const double waited = std::chrono::duration<double>(now - (*it)->t_submit).count();
+            const double key = (*it)->work / (1.0 + 10.0 * waited);
+            if (it == sv->pending.begin() || key < best) {
+              best = key;
+              pick = it;
+            }
+          }
+        }
+        Job* jb = *pick;
         if (sv->mem_used + jb->bytes > sv->cfg.mem_budget && sv->active > 0) break;
-        sv->pending.pop_front();
+        sv->pending.erase(pick);
         sv->mem_used += jb->bytes;
         sv->peak_mem = std::max(sv->peak_mem, sv->mem_used);
+        jb->behind = sv->active;
         sv->active += 1;
         sv->peak_active = std::max(sv->peak_active, sv->active);
         admit.push_back(jb);
@@ -169,7 +241,7 @@ void scheduler(ig_server* sv) {
     for (Job* jb : admit) {
       jb->t_admit = Clock::now();
       std::string err;
-      const ig_status st = admit_job(jb, &err);
+      const ig_status st = admit_job(sv, jb, &err);
       if (st != IG_OK) finish_job(sv, jb, st, err);
       else running.push_back(jb);
     }
@@ -294,6 +366,15 @@ ig_status intergrams_server_submit(ig_server* sv, const ig_params* p, const void
   jb->offsets.assign(offsets, offsets + (size_t)m + 1);
   jb->m = m;
   jb->bytes = bytes;
+  {
+    const uint32_t b = std::min(p->base_n, p->n);
+    const double passes = (double)(p->n - b + 1);
+    const double sym_bytes = (double)offsets[m] * (p->symbol_bits == 2 ? 0.25 : 1.0);
+    const double sigma = p->symbol_bits == 2 ? 4.0 : 256.0;
+    // the corpus is streamed once per pass; each candidate pass also reads
+    // its sigma * Z counters a few times in the selection
+    jb->work = sym_bytes * passes + (passes - 1) * 3.0 * 2.0 * sigma * (double)p->candidates;
+  }
   jb->t_submit = Clock::now();
   sv->jobs[jb->id] = jb;
   sv->pending.push_back(jb);
@@ -357,6 +438,7 @@ void intergrams_server_destroy(ig_server* sv) {
   }
   if (sv->worker.joinable()) sv->worker.join();
   for (auto& kv : sv->jobs) delete kv.second;
+  for (auto& kv : sv->pinned_free) cudaFreeHost(kv.second);
   delete sv;
 }
 

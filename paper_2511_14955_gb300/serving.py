@@ -61,11 +61,16 @@ def job_stream(n_jobs: int, rate: float, n_corpora: int, seed: int, ns=(4, 8, 16
 
 
 def run_stream(pool, jobs, *, max_active: int, mem_budget: int = 0, z_factor: int = 4, base_n: int = 3,
-               tuning: dict | None = None, keep_results: bool = False):
-    """Submit every job at its arrival time; returns latency and throughput figures."""
+               tuning: dict | None = None, keep_results: bool = False, fifo: bool = False,
+               policy: str | None = None):
+    """Submit every job at its arrival time; returns latency and throughput
+    figures. ``policy``: "least_work_first" (the server's default),
+    "oldest_first" or "fifo" (arrival order on default-priority streams, the
+    one-job-per-launch baseline; also ``fifo=True``)."""
     results = {}
     lat = [None] * len(jobs)
-    with binding.Server(mem_budget=mem_budget, max_active=max_active) as sv:
+    policy = policy or ("fifo" if fifo else "least_work_first")
+    with binding.Server(mem_budget=mem_budget, max_active=max_active, policy=policy) as sv:
         ids = [None] * len(jobs)
         ready = threading.Event()
         errors = []
@@ -101,7 +106,8 @@ def run_stream(pool, jobs, *, max_active: int, mem_budget: int = 0, z_factor: in
         raise RuntimeError(f"{len(errors)} jobs failed, first: {errors[0]}")
     scanned = sum(int(pool[jb.corpus][1][-1]) * (jb.n - min(base_n, jb.n) + 1) for jb in jobs)
     lat_ms = np.array(lat) * 1e3
-    out = {"jobs": len(jobs), "max_active": max_active, "p50_ms": float(np.percentile(lat_ms, 50)),
+    out = {"jobs": len(jobs), "max_active": max_active, "policy": policy,
+           "p50_ms": float(np.percentile(lat_ms, 50)),
            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
            "makespan_s": makespan, "scanned_gb": scanned / 1e9, "gbps": scanned / makespan / 1e9,
            "peak_active": stats["peak_active"], "peak_mem_gb": stats["peak_mem"] / 1e9}

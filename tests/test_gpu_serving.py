@@ -80,3 +80,29 @@ def test_job_larger_than_budget_is_rejected(pool):
         with pytest.raises(B.IntergramsError) as ei:
             sv.submit(data, off, n=8, k=512, candidates=2048)
         assert ei.value.status == -2
+
+
+def test_least_work_first_admits_the_small_job_ahead():
+    """With one slot busy, a large job and then a small job queue up: the
+    default policy admits the small one first, arrival order the large one;
+    results are the same either way."""
+    import time
+    big = serving.make_pool(1, seed=41, median_bytes=60e6, sigma=0.01, lo_bytes=50_000_000, hi_bytes=70_000_000)[0]
+    small = serving.make_pool(1, seed=42, median_bytes=3e5, sigma=0.01, lo_bytes=200_000, hi_bytes=400_000)[0]
+    order = {}
+    rows = {}
+    for fifo in (False, True):
+        with B.Server(max_active=1, fifo=fifo) as sv:
+            first = sv.submit(*big, n=16, k=1024, candidates=4096)      # occupies the slot
+            t_b = time.perf_counter()
+            b = sv.submit(*big, n=8, k=1024, candidates=4096)
+            t_s = time.perf_counter()
+            s = sv.submit(*small, n=8, k=1024, candidates=4096)
+            done = {}
+            for name, jid, t in (("small", s, t_s), ("big", b, t_b), ("first", first, 0.0)):
+                keys, counts, lat = sv.wait(jid)
+                rows[(fifo, name)] = (keys.tobytes(), counts.tolist())
+                done[name] = lat + t                  # completion on the perf_counter clock
+            order[fifo] = done["small"] < done["big"]
+    assert order[False] and not order[True]
+    assert rows[(False, "small")] == rows[(True, "small")] and rows[(False, "big")] == rows[(True, "big")]
