@@ -142,6 +142,17 @@ typedef struct {
   uint32_t tile_cache_hint;  /* L2 policy of the corpus tile copies: 1 = none, 2 = evict first (read
                                 once per pass, so the counters, spill lists and tables keep L2);
                                 0 = default (2) */
+  uint32_t prefetch_tiles;   /* corpus tiles of a sequence prefetched into L2 ahead of their copies
+                                to shared memory: value - 1 tiles (1 = none, up to 9); 0 = default
+                                (none) */
+  uint32_t spill_dedupe;     /* Eq. 2 dedupe of the slots a sequence spilled from its shared-memory
+                                set: 2 = counting-sort into buckets by 32-slot word (interleaved),
+                                then one bit vector per bucket in the set's shared memory; 1 = hash
+                                partition (one or two levels) and a hash set per bucket; 0 = default
+                                (2) */
+  uint32_t spill_min_fill;   /* with spill_dedupe 2: a sequence's spills take the bit-vector path
+                                when they fill each of its buckets with at least value - 1 entries
+                                on average (fewer: the hash path); 0 = default (512) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

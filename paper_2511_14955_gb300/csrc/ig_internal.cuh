@@ -136,6 +136,10 @@ struct ScanArgs {
   uint32_t tile2;              // word offset of the second tile buffer in dynamic smem (0 = one buffer)
   uint32_t stall_tiles;        // test hook: tile barriers are never armed, so tile waits run out
   uint32_t tile_evict_first;   // corpus tile copies carry an L2 evict-first policy
+  uint32_t prefetch_tiles;     // tiles of the sequence prefetched into L2 ahead of the copies (0 = none)
+  uint64_t nslots;             // slots (counters) of this pass
+  uint32_t range_dedupe;       // Eq. 2 spill dedupe by word bucket and bit vector (else hash partition + set)
+  uint32_t range_min_fill;     // ... for sequences whose spills fill each bucket with at least this many
   PassCtl* ctl;
 };
 

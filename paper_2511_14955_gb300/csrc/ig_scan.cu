@@ -246,6 +246,20 @@ __device__ __forceinline__ void stage_issue(const ScanArgs& a, const TileGeom& g
   }
 }
 
+// Prefetch tile `g`'s bytes inside the corpus' 16-byte aligned extent into
+// L2 (one bulk prefetch by thread 0; no shared memory, nothing to wait for),
+// so that the tile's later bulk copy reads L2: with one copy in flight per
+// CTA, a copy from HBM per tile left streaming passes latency-bound.
+__device__ __forceinline__ void prefetch_tile(const ScanArgs& a, const TileGeom& g) {
+  if (threadIdx.x != 0 || a.stall_tiles) return;
+  const uintptr_t lo_ok = reinterpret_cast<uintptr_t>(a.data), hi_ok = lo_ok + a.data_bytes;
+  const uintptr_t lo16 = (lo_ok + 15) & ~(uintptr_t)15, hi16 = hi_ok & ~(uintptr_t)15;
+  const uintptr_t ia = g.al > lo16 ? g.al : lo16;
+  const uintptr_t ie = (g.al + g.nbytes) < hi16 ? (g.al + g.nbytes) : hi16;
+  if (ie > ia)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ia), "r"((uint32_t)(ie - ia)) : "memory");
+}
+
 // tile_key for keys of at most 32 bits (two words).
 template <int SB>
 __device__ __forceinline__ uint64_t tile_key32(const uint32_t* tile, uint32_t o, uint32_t j) {
@@ -514,6 +528,106 @@ __device__ __forceinline__ uint32_t bucket_bits(uint32_t n, uint32_t cap, uint32
   return kb;
 }
 
+// Counting-sort src[lo, hi) into dst[lo, hi) by the low kb bits of the
+// slot's 32-slot word: bucket b holds the slots whose word index is b mod
+// 2^kb and ends up in dst[bnd[b], bnd[b + 1]). Interleaving the words over
+// the buckets spreads slots that cluster in a few ranges (rank order puts
+// the frequent prefixes first) evenly, so no bucket counter is hammered.
+__device__ void partition_by_word(const uint32_t* src, uint32_t* dst, uint32_t lo, uint32_t hi, uint32_t kb,
+                                  uint32_t* bnd, uint32_t* cur) {
+  __shared__ uint32_t s_wt[33];
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x, K = 1u << kb, mask = K - 1u;
+  for (uint32_t b = tid; b < K; b += nthr) bnd[b] = 0;
+  __syncthreads();
+  for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
+    uint32_t v[kBatch];
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k)
+      if (i0 + k * nthr < hi) atomicAdd(bnd + ((v[k] >> 5) & mask), 1u);
+  }
+  __syncthreads();
+  const uint32_t per = (K + nthr - 1) / nthr, b0 = tid * per, b1 = b0 + per < K ? b0 + per : K;
+  uint32_t mine = 0;
+  for (uint32_t b = b0; b < b1; ++b) mine += bnd[b];
+  uint32_t total = 0;
+  uint32_t run = lo + block_excl_sum(mine, s_wt, total);
+  __syncthreads();
+  for (uint32_t b = b0; b < b1; ++b) {
+    const uint32_t c = bnd[b];
+    bnd[b] = run;
+    cur[b] = run;
+    run += c;
+  }
+  if (tid == 0) bnd[K] = hi;
+  __syncthreads();
+  for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
+    uint32_t v[kBatch];
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k)
+      if (i0 + k * nthr < hi) dst[atomicAdd(cur + ((v[k] >> 5) & mask), 1u)] = v[k];
+  }
+  __syncthreads();
+}
+
+// Exact dedupe of src[lo, hi) (the slots of one bucket: word index = b mod
+// 2^kb) with a bit vector in shared memory (the per-sequence set's words, all
+// zero on entry and on exit): slot v is bit v mod 32 of word v >> (5 + kb);
+// the thread that sets a slot's bit registers it. The bits are cleared again
+// word by word after use, or all at once when the bucket holds more entries
+// than the vector has words.
+__device__ void bitmap_bucket(const ScanArgs& a, const LogState& lg, const uint32_t* src, uint32_t lo, uint32_t hi,
+                              uint32_t kb, uint32_t* bm, uint32_t bm_words, unsigned long long& my_regs) {
+  const uint32_t tid = threadIdx.x, nthr = blockDim.x, ws = 5u + kb;
+  if (a.rlog) {
+    log_room(a, lg, hi - lo);
+    __syncthreads();
+  }
+  for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
+    uint32_t v[kBatch];
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kBatch; ++k) {
+      if (i0 + k * nthr < hi) {
+        const uint32_t bit = 1u << (v[k] & 31u);
+        if (!(atomicOr(bm + (v[k] >> ws), bit) & bit)) {
+          ++my_regs;
+          register_slot(a, lg, v[k]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (hi - lo >= bm_words) {
+    for (uint32_t i = tid; i < bm_words; i += nthr) bm[i] = 0u;
+  } else {
+    for (uint32_t i = lo + tid; i < hi; i += nthr) bm[src[i] >> ws] = 0u;
+  }
+  __syncthreads();
+}
+
+// Phase 2 by bit vector: the spilled slots of one sequence (S entries,
+// duplicates included, disjoint from the slots already in the set) are
+// counting-sorted into K = 2^kb buckets by their 32-slot word index, K just
+// large enough that a bucket's slots fit one bit vector in the set's shared
+// memory, and each bucket is deduplicated with that bit vector. One
+// partition level, no hashing, no probing.
+__device__ void dedupe_spills_by_word(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t kb, uint32_t* sset,
+                                      uint32_t* scratch, uint32_t* list, uint32_t* part,
+                                      unsigned long long& my_regs) {
+  const uint32_t words = 1u << a.sset_log2, K = 1u << kb;
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sset[i] = 0u;  // the set becomes the bit vector
+  partition_by_word(list, part, 0, S, kb, scratch, scratch + K + 1);
+  for (uint32_t b = 0; b < K; ++b) {
+    const uint32_t lo = scratch[b], hi = scratch[b + 1];
+    if (hi > lo) bitmap_bucket(a, lg, part, lo, hi, kb, sset, words, my_regs);  // uniform across the CTA
+  }
+}
+
 // Phase 2: the spilled slots of one sequence (S entries, duplicates
 // included, disjoint from the slots already in the set) are hash-partitioned
 // (at most two levels, bucket tables in the free tile buffer) into buckets of
@@ -525,6 +639,16 @@ __device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S,
   if (S <= fit) {
     insert_range(a, lg, list, 0, S, sset, my_regs);
     return;
+  }
+  if (a.range_dedupe && a.nslots) {
+    // buckets: the fewest (a power of two) whose words fit the bit vector
+    uint32_t kb = 0;
+    while ((a.nslots + 31) / 32 > ((uint64_t)cap << kb)) ++kb;
+    // worth its two barriers per bucket once the buckets are well filled
+    if (2 * (1ull << kb) + 1 <= scratch_words && ((uint64_t)S >> kb) >= a.range_min_fill) {
+      dedupe_spills_by_word(a, lg, S, kb, sset, scratch, list, part, my_regs);
+      return;
+    }
   }
   const uint32_t half = scratch_words / 2;
   uint32_t kbmax = 0;
@@ -637,6 +761,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     // second buffer); tile 0 is issued here, tile t + 1 once tile t arrived
     __syncthreads();  // the previous sequence is done with both buffers
     stage_issue(a, tile_geom<SB>(a, s0, W, 0, tile_windows, j), reinterpret_cast<uint8_t*>(tile0), &s_bar[0]);
+    for (uint32_t d = 1; d <= a.prefetch_tiles; ++d)
+      if ((uint64_t)d * tile_windows < W) prefetch_tile(a, tile_geom<SB>(a, s0, W, (uint64_t)d * tile_windows, tile_windows, j));
     uint32_t tix = 0;
     for (uint64_t w0 = 0; w0 < W; w0 += tile_windows, ++tix) {
       const TileGeom g = tile_geom<SB>(a, s0, W, w0, tile_windows, j);
@@ -661,6 +787,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
       if (a.tile2 && w0 + tile_windows < W)
         stage_issue(a, tile_geom<SB>(a, s0, W, w0 + tile_windows, tile_windows, j),
                     reinterpret_cast<uint8_t*>(bsel ? tile0 : tile1), s_bar + (bsel ^ 1u));
+      if (a.prefetch_tiles && w0 + (uint64_t)(a.prefetch_tiles + 1) * tile_windows < W)
+        prefetch_tile(a, tile_geom<SB>(a, s0, W, w0 + (uint64_t)(a.prefetch_tiles + 1) * tile_windows, tile_windows, j));
 
       const uint32_t wb = tid * R;
       if (BASE) {

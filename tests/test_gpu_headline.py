@@ -41,7 +41,7 @@ def headline_corpus(seed=21, short_bytes=200_000_000):
 @pytest.fixture(scope="module")
 def corpus():
     data, off = headline_corpus()
-    assert (np.diff(off.astype(np.int64)) >= 4 << 20).sum() == len(LONG) and len(off) - 1 >= 200
+    assert (np.diff(off.astype(np.int64)) >= 4 << 20).sum() >= len(LONG) and len(off) - 1 >= 200
     return data, off
 
 
