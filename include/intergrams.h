@@ -95,11 +95,15 @@ typedef struct {
   uint32_t hot_log2;         /* log2 entries of the shared-memory cache of the most frequent
                                 candidates in front of the probe table (6..13; default 11) */
   uint32_t chain_from;       /* first pass run from the previous pass's survivor lists instead of a
-                                corpus scan (default: none); passes whose (j-1)-gram exceeds 64 bits
-                                always run this way */
-  uint32_t list_pct;         /* capacity of each survivor list, percent of the corpus symbols
-                                (default: 100 when two full lists fit in 25% of the free device
-                                memory, else 25; exceeding it returns IG_ETABLE_FULL) */
+                                corpus scan (default: n - 1 for bytes when n >= base_n + 4, the
+                                passes where few windows survive, else none; n + 1 = none); passes
+                                whose (j-1)-gram exceeds 64 bits always run this way */
+  uint32_t list_pct;         /* initial capacity of each survivor list, percent of the corpus
+                                symbols (default: 100 when two full lists fit in 25% of the free
+                                device memory, else 25). A pass that needs more makes
+                                intergrams_run / intergrams_pass grow both lists to what was asked
+                                for and run the job again; IG_ETABLE_FULL only when the device has
+                                no memory for them (the plan then refuses further passes) */
   /* Registration log of the candidate passes: a count increment is appended to
      a log chunk of its counter range and the log is counted range by range
      after the scan, so the increments of any moment fall in one range of the

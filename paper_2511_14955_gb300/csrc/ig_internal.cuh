@@ -61,6 +61,7 @@ struct PassCtl {
   uint32_t gset_clear;               // epochs wrapped: clear the dedupe sets before the scan
   uint32_t rlog_next;                // registration-log chunks handed out in this pass
   unsigned long long list_used;      // entries reserved in this pass's survivor list
+  unsigned long long list_need;      // largest reservation end any pass asked for (sticky)
 };
 
 struct ScanArgs {

@@ -984,6 +984,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
           if (tid < nruns) {
             const uint32_t rn = (qn - tid * kRunChunk) < kRunChunk ? qn - tid * kRunChunk : kRunChunk;
             unsigned long long base = atomicAdd(&a.ctl->list_used, (unsigned long long)rn);
+            atomicMax(&a.ctl->list_need, base + rn);
             if (base + rn > a.list_cap) {
               atomicOr(&a.ctl->status, kStListFull);
               base = ~0ull;
@@ -1228,6 +1229,7 @@ __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
         unsigned long long base = ~0ull;
         if (total) {
           base = atomicAdd(&a.ctl->list_used, (unsigned long long)total);
+          atomicMax(&a.ctl->list_need, base + total);
           if (base + total > a.list_cap) {
             atomicOr(&a.ctl->status, kStListFull);
             base = ~0ull;

@@ -171,14 +171,51 @@ def test_chain_passes_after_rank_select_passes(mode):
                      tuning=dict(chain_from=5, dense_prefix=4, rs_depth=3))
 
 
-def test_list_capacity_exceeded_is_reported():
+@pytest.mark.parametrize("graph", [False, True])
+def test_survivor_lists_grow_and_the_job_replays(graph):
+    """Survivor lists far too small for the job: the plan grows them to what
+    the passes asked for and replays, so the result is exact (pass by pass
+    and as one captured graph, which is captured again for the new lists)."""
     data, off, _ = synth.make_corpus("markov_2mb", m=10, seed=3)
     d, o = dev(data, off)
+    ek, ec = O.intergrams(data, off, 6, 10, 4000, base_n=1)
+    with B.Plan(d, o, n=6, k=10, candidates=4000, base_n=1, graph=graph,
+                tuning=dict(chain_from=3, list_pct=1)) as pl:
+        for _ in range(2):
+            pl.rewind()
+            pl.run()
+            keys, counts, _ = pl.topk()
+            assert np.array_equal(keys, ek) and np.array_equal(counts, ec)
+    with B.Plan(d, o, n=6, k=10, candidates=4000, base_n=1, tuning=dict(chain_from=3, list_pct=1)) as pl:
+        for j in range(1, 7):
+            assert pl.step() == j
+            keys, counts, _ = pl.topk()
+            wk, wc = O.intergrams(data, off, 6, 10, 4000, base_n=1, stop_j=j)
+            assert np.array_equal(keys, wk) and np.array_equal(counts, wc), j
+
+
+def test_list_growth_failing_is_reported():
+    """No memory for the larger lists (the growth allocation made to fail on
+    the host): IG_ETABLE_FULL, the plan refuses further passes, and nothing
+    leaks once it is freed."""
+    data, off, _ = synth.make_corpus("markov_2mb", m=10, seed=3)
+    d, o = dev(data, off)
+    live0 = B.test_fail_alloc(0)
     pl = B.Plan(d, o, n=6, k=10, candidates=4000, base_n=1, tuning=dict(chain_from=3, list_pct=1))
-    with pytest.raises(B.IntergramsError) as ei:
-        pl.run()
-    assert ei.value.status == -3
-    pl.close()
+    B.test_fail_alloc(1)                 # the next allocation: the first grown list
+    try:
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.run()
+        assert ei.value.status == -3
+        B.test_fail_alloc(0)
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.rewind()
+            pl.run()
+        assert ei.value.status == -7
+    finally:
+        B.test_fail_alloc(0)
+        pl.close()
+    assert B.test_fail_alloc(0) == live0
 
 
 def test_edge_cases():
