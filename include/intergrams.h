@@ -157,6 +157,9 @@ typedef struct {
   uint32_t spill_min_fill;   /* with spill_dedupe 2: a sequence's spills take the bit-vector path
                                 when they fill each of its buckets with at least value - 1 entries
                                 on average (fewer: the hash path); 0 = default (512) */
+  uint32_t carry_slots;      /* rank/select passes after the first read each window's slot of the
+                                previous pass from a per-symbol array (one lookup instead of one per
+                                level; 4 bytes per corpus symbol): 2 = on, 1 or 0 (default) = off */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -132,6 +132,12 @@ struct ScanArgs {
   // prefix's byte-order id follows level by level (0 = the probe table)
   const uint2* rs[kMaxRsLevels];
   uint32_t rs_depth;
+  // carried slots of rank/select passes: carry[p] = the slot the window
+  // starting at corpus symbol p got in the previous pass (read when carry_in:
+  // one lookup, at the last level, instead of rs_depth), and the slot it
+  // gets in this pass (written for survivors when carry_out)
+  uint32_t* carry;
+  uint32_t carry_in, carry_out;
   uint32_t base_len;
   uint32_t set_probes;         // bounded probe length of the shared-memory dedupe set (1..8)
   uint32_t tile2;              // word offset of the second tile buffer in dynamic smem (0 = one buffer)

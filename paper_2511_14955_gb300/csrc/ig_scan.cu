@@ -1021,7 +1021,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             if (qi < q1) {
               const uint32_t w = queue[qi];
               wl[k] = (w << 8) | tile_sym<SB>(tile, sym_off + w + j - 1);
-              if (a.rs_depth) {  // level 0: the base-length prefix; its word and the count before it
+              if (a.rs_depth && a.carry_in) {  // the last level: the window's slot in the previous pass
+                prefix[k] = a.carry[gsym + w];
+                const uint2 pe = __ldg(a.rs[a.rs_depth - 1] + (prefix[k] >> 5));
+                e[k] = make_uint4(pe.x, pe.y, 0, 0);
+              } else if (a.rs_depth) {  // level 0: the base-length prefix; its word and the count before it
                 prefix[k] = tile_key32<SB>(tile, sym_off + w, a.base_len);
                 const uint2 pe = __ldg(a.rs[0] + (prefix[k] >> 5));
                 e[k] = make_uint4(pe.x, pe.y, 0, 0);
@@ -1041,7 +1045,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             // base_len + L symbols at level L is its position among the
             // selected slots of pass base + L (all levels' loads of a round
             // are issued together)
-            for (uint32_t L = 0;; ++L) {
+            for (uint32_t L = a.carry_in ? a.rs_depth - 1 : 0;; ++L) {
 #pragma unroll
               for (uint32_t k = 0; k < kProbeBatch; ++k) {
                 if (wl[k] == 0xFFFFFFFFu || id[k] == kDead) continue;
@@ -1070,6 +1074,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             const uint32_t qi = qb + k * nthr;
             const uint32_t w = wl[k] >> 8, last = wl[k] & 255u;
             const uint32_t slot = (id[k] << SB) | last;
+            if (a.carry_out) a.carry[gsym + w] = slot;
             if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
             if (a.list_out) {
               const uint32_t r = qi / kRunChunk;

@@ -113,6 +113,11 @@ def test_dna_reduced(mode):
     dict(set_probes=1, smem_set_log2=11),                                     # one-probe set, many spills
     dict(set_probes=8),
     dict(tile_cache_hint=1, tile_buffers=1),                                  # plain tile copies, one buffer
+    dict(prefetch_tiles=4),                                                   # tiles prefetched into L2
+    dict(spill_dedupe=1, smem_set_log2=10),                                   # spills by hash partition
+    dict(spill_min_fill=1, smem_set_log2=10),                                 # spills by bit vector, always
+    dict(dense_prefix=4, rs_depth=3, carry_slots=2),                          # carried slots
+    dict(chain_from=6),                                                       # no chain passes
 ])
 def test_results_do_not_depend_on_tuning(tuning):
     data, off, _ = synth.make_corpus("markov_2mb", seed=2)
