@@ -165,7 +165,14 @@ typedef struct {
 typedef struct ig_plan ig_plan;
 
 /*
- * intergrams_plan - validate the inputs and build a plan for one corpus.
+ * intergrams_plan - validate the inputs and build a plan for one corpus: the
+ * problem of Sec. 2 - m sequences s_1..s_m over an alphabet, a length n and a
+ * count k - with the frequency of Eq. 2 (count_mode 0: once per sequence
+ * containing the n-gram) or Eq. 1 (count_mode 1: every occurrence), solved by
+ * the passes of Algorithm 3 (Sec. 7) from a dense pass of Algorithm 2 (Sec. 6)
+ * over base_n-grams; Z = candidates plays the paper's zk. The trailing
+ * `tuning` argument is this library's own (the knobs only change speed and
+ * memory, never the result).
  *   p        : parameters (copied).
  *   data     : the concatenated sequences (device pointer; host pointer with
  *              IG_F_HOST_INPUT). Bytes for symbol_bits 8; packed bases for 2.
@@ -485,10 +492,13 @@ ig_status intergrams_server_stats(ig_server* sv, ig_server_stats* out);
 /* Finish every queued job, stop the scheduler and free the server. */
 void intergrams_server_destroy(ig_server* sv);
 
-/* Release every resource of the plan (stream-ordered frees). NULL is ignored. */
+/* Release every resource of the plan (stream-ordered frees). NULL is ignored.
+ * No counterpart in the paper (resource management of this library). */
 void intergrams_free(ig_plan* pl);
 
-/* Message describing the last error on the calling thread ("" if none). */
+/* Message describing the last error on the calling thread ("" if none). No
+ * counterpart in the paper (error reporting of this library: no exception
+ * crosses the ABI, every call returns an ig_status). */
 const char* intergrams_last_error(void);
 
 /*
