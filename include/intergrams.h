@@ -160,6 +160,9 @@ typedef struct {
   uint32_t carry_slots;      /* rank/select passes after the first read each window's slot of the
                                 previous pass from a per-symbol array (one lookup instead of one per
                                 level; 4 bytes per corpus symbol): 2 = on, 1 or 0 (default) = off */
+  uint32_t set_max_windows;  /* Eq. 2: a sequence with more windows than this sends every survivor
+                                straight to its spill list, skipping the shared-memory set (0 =
+                                default: never) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

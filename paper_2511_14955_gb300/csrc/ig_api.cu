@@ -387,6 +387,7 @@ uint32_t enqueue_scan(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.nslots = ns;
   a.range_dedupe = pl->t.spill_dedupe != 1u;
   a.range_min_fill = pl->t.spill_min_fill ? pl->t.spill_min_fill - 1u : 512u;
+  a.set_max_windows = pl->t.set_max_windows;
   if (base) {  // the base pass's own tile and set; no queue
     a.words_per_thread = pl->base_wpt;
     a.sset_log2 = pl->base_sset_log2;

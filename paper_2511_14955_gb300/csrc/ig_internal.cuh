@@ -147,6 +147,7 @@ struct ScanArgs {
   uint64_t nslots;             // slots (counters) of this pass
   uint32_t range_dedupe;       // Eq. 2 spill dedupe by word bucket and bit vector (else hash partition + set)
   uint32_t range_min_fill;     // ... for sequences whose spills fill each bucket with at least this many
+  uint32_t set_max_windows;    // Eq. 2: sequences with more windows skip the shared-memory set (0 = never)
   PassCtl* ctl;
 };
 

@@ -742,6 +742,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     const uint64_t W = L - j + 1;
     const uint32_t epoch = epoch_base + seq + 1;
     const uint32_t sprobes = a.set_probes;
+    // a sequence this long sends every survivor straight to its spill list
+    // (the set would only hold a small share of its slots)
+    const bool no_set = a.set_max_windows && W > a.set_max_windows;
     uint32_t slog = 0, glog = 0;
     if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       uint32_t need = ceil_log2_u64(2 * W);
@@ -815,7 +818,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
-                const int r = sset_try_insert(sset, slog, slot, sprobes);
+                const int r = no_set ? 2 : sset_try_insert(sset, slog, slot, sprobes);
                 count_it = (r == 1);
                 if (r == 2) spill_push(spill_list, &s_nspill, slot);
               } else {
@@ -898,7 +901,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
                 if (bm) {
                   count_it = bitmap_first(bm, slot);
                 } else if (spill_list) {
-                  const int r = sset_try_insert(sset, slog, slot, sprobes);
+                  const int r = no_set ? 2 : sset_try_insert(sset, slog, slot, sprobes);
                   count_it = (r == 1);
                   if (r == 2) spill_push(spill_list, &s_nspill, slot);
                 } else {
@@ -1088,7 +1091,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
-                const int r = sset_try_insert(sset, slog, slot, sprobes);
+                const int r = no_set ? 2 : sset_try_insert(sset, slog, slot, sprobes);
                 count_it = (r == 1);
                 if (r == 2) spill_push(spill_list, &s_nspill, slot);
               } else {
