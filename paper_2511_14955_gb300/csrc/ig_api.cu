@@ -637,6 +637,15 @@ ig_status plan_last_status(ig_plan* pl) {
   return IG_OK;
 }
 
+// After plan_last_status reported a survivor list out of room (and nothing
+// else): grow the lists and rewind, so the job runs again from its first
+// pass. False when that was not the failure or the lists could not grow.
+bool plan_regrow_and_restart(ig_plan* pl) {
+  if (!list_full_only(pl)) return false;
+  if (grow_lists(pl) != IG_OK) return false;
+  return intergrams_rewind(pl) == IG_OK;
+}
+
 // Enqueue the final top-k into PINNED host buffers, and `ev`; *rows is known
 // at once (from the last status).
 ig_status plan_enqueue_topk(ig_plan* pl, uint8_t* keys_host, uint64_t* counts_host, uint32_t cap, uint32_t* rows,

@@ -38,6 +38,7 @@ bool plan_passes_done(const ig_plan* pl);
 uint32_t plan_row_bytes(const ig_plan* pl);
 ig_status plan_enqueue_next(ig_plan* pl, cudaEvent_t ev);
 ig_status plan_last_status(ig_plan* pl);
+bool plan_regrow_and_restart(ig_plan* pl);
 ig_status plan_enqueue_topk(ig_plan* pl, uint8_t* keys_host, uint64_t* counts_host, uint32_t cap, uint32_t* rows,
                             cudaEvent_t ev);
 void set_last_error(const std::string& msg);
@@ -263,7 +264,19 @@ void scheduler(ig_server* sv) {
           finish_job(sv, jb, IG_ECUDA, cudaGetErrorString(q));
           finished = true;
         } else if (jb->state == kPasses) {
-          const ig_status st = ig::plan_last_status(jb->plan);
+          ig_status st = ig::plan_last_status(jb->plan);
+          if (st == IG_ETABLE_FULL && ig::plan_regrow_and_restart(jb->plan)) {
+            // its survivor lists grew: charge the job's new size, run it again
+            uint64_t b = 0;
+            intergrams_plan_device_bytes(jb->plan, &b);
+            std::lock_guard<std::mutex> lock(sv->mu);
+            if (b > jb->bytes) {
+              sv->mem_used += b - jb->bytes;
+              sv->peak_mem = std::max(sv->peak_mem, sv->mem_used);
+              jb->bytes = b;
+            }
+            st = IG_OK;
+          }
           if (st != IG_OK) {
             finish_job(sv, jb, st, intergrams_last_error());
             finished = true;

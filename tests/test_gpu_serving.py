@@ -106,3 +106,14 @@ def test_least_work_first_admits_the_small_job_ahead():
             order[fifo] = done["small"] < done["big"]
     assert order[False] and not order[True]
     assert rows[(False, "small")] == rows[(True, "small")] and rows[(False, "big")] == rows[(True, "big")]
+
+
+def test_served_job_grows_its_survivor_lists(pool):
+    """A served job whose survivor lists are far too small: the server grows
+    them, runs the job again and returns the exact rows."""
+    data, off = pool[0]
+    want = alone(pool, serving.Job(0.0, 0, 8, 256))
+    with B.Server(max_active=2) as sv:
+        jid = sv.submit(data, off, n=8, k=256, candidates=1024, base_n=3, tuning=dict(chain_from=5, list_pct=1))
+        keys, counts, _ = sv.wait(jid, timeout_s=120)
+    assert np.array_equal(counts, want[1]) and np.array_equal(keys, want[0])
