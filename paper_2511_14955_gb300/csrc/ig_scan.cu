@@ -534,20 +534,22 @@ __device__ __forceinline__ uint32_t bucket_bits(uint32_t n, uint32_t cap, uint32
 // the buckets spreads slots that cluster in a few ranges (rank order puts
 // the frequent prefixes first) evenly, so no bucket counter is hammered.
 __device__ void partition_by_word(const uint32_t* src, uint32_t* dst, uint32_t lo, uint32_t hi, uint32_t kb,
-                                  uint32_t* bnd, uint32_t* cur) {
+                                  uint32_t* bnd, uint32_t* cur, const uint32_t* counts) {
   __shared__ uint32_t s_wt[33];
   const uint32_t tid = threadIdx.x, nthr = blockDim.x, K = 1u << kb, mask = K - 1u;
-  for (uint32_t b = tid; b < K; b += nthr) bnd[b] = 0;
+  for (uint32_t b = tid; b < K; b += nthr) bnd[b] = counts ? counts[b] : 0u;
   __syncthreads();
-  for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
-    uint32_t v[kBatch];
+  if (!counts) {  // (counted already while the slots were spilled)
+    for (uint32_t i0 = lo + tid; i0 < hi; i0 += kBatch * nthr) {
+      uint32_t v[kBatch];
 #pragma unroll
-    for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
+      for (uint32_t k = 0; k < kBatch; ++k) v[k] = i0 + k * nthr < hi ? src[i0 + k * nthr] : 0u;
 #pragma unroll
-    for (uint32_t k = 0; k < kBatch; ++k)
-      if (i0 + k * nthr < hi) atomicAdd(bnd + ((v[k] >> 5) & mask), 1u);
+      for (uint32_t k = 0; k < kBatch; ++k)
+        if (i0 + k * nthr < hi) atomicAdd(bnd + ((v[k] >> 5) & mask), 1u);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const uint32_t per = (K + nthr - 1) / nthr, b0 = tid * per, b1 = b0 + per < K ? b0 + per : K;
   uint32_t mine = 0;
   for (uint32_t b = b0; b < b1; ++b) mine += bnd[b];
@@ -617,11 +619,11 @@ __device__ void bitmap_bucket(const ScanArgs& a, const LogState& lg, const uint3
 // memory, and each bucket is deduplicated with that bit vector. One
 // partition level, no hashing, no probing.
 __device__ void dedupe_spills_by_word(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t kb, uint32_t* sset,
-                                      uint32_t* scratch, uint32_t* list, uint32_t* part,
+                                      uint32_t* scratch, uint32_t* list, uint32_t* part, const uint32_t* counts,
                                       unsigned long long& my_regs) {
   const uint32_t words = 1u << a.sset_log2, K = 1u << kb;
   for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sset[i] = 0u;  // the set becomes the bit vector
-  partition_by_word(list, part, 0, S, kb, scratch, scratch + K + 1);
+  partition_by_word(list, part, 0, S, kb, scratch, scratch + K + 1, counts);
   for (uint32_t b = 0; b < K; ++b) {
     const uint32_t lo = scratch[b], hi = scratch[b + 1];
     if (hi > lo) bitmap_bucket(a, lg, part, lo, hi, kb, sset, words, my_regs);  // uniform across the CTA
@@ -634,7 +636,8 @@ __device__ void dedupe_spills_by_word(const ScanArgs& a, const LogState& lg, uin
 // at most half the set's capacity, and each bucket is deduplicated exactly.
 __device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t* sset, uint32_t* scratch,
                               uint32_t scratch_words, uint32_t* list, uint32_t* part,
-                              unsigned long long& my_regs) {
+                              unsigned long long& my_regs, const uint32_t* bucket_counts = nullptr,
+                              uint32_t counted_kb = 0xFFFFFFFFu) {
   const uint32_t cap = 1u << a.sset_log2, fit = cap / 2;
   if (S <= fit) {
     insert_range(a, lg, list, 0, S, sset, my_regs);
@@ -646,7 +649,8 @@ __device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S,
     while ((a.nslots + 31) / 32 > ((uint64_t)cap << kb)) ++kb;
     // worth its two barriers per bucket once the buckets are well filled
     if (2 * (1ull << kb) + 1 <= scratch_words && ((uint64_t)S >> kb) >= a.range_min_fill) {
-      dedupe_spills_by_word(a, lg, S, kb, sset, scratch, list, part, my_regs);
+      dedupe_spills_by_word(a, lg, S, kb, sset, scratch, list, part, kb == counted_kb ? bucket_counts : nullptr,
+                            my_regs);
       return;
     }
   }
@@ -680,6 +684,14 @@ template <int SB, bool BASE>
 __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_item, s_nspill, s_qn;
+  // spills per bit-vector bucket of the sequence, counted as they are
+  // pushed (K = 2^kb buckets of 32-slot words; kb as the dedupe picks it)
+  constexpr uint32_t kMaxCountedBuckets = 128;
+  __shared__ uint32_t s_bcnt[kMaxCountedBuckets];
+  uint32_t spill_kb = 0;
+  while ((a.nslots + 31) / 32 > ((uint64_t)1 << (a.sset_log2 + spill_kb))) ++spill_kb;
+  const bool count_buckets = a.range_dedupe && (1u << spill_kb) <= kMaxCountedBuckets;
+  const uint32_t bmask = (1u << spill_kb) - 1u;
   __shared__ unsigned long long s_run_base[kMaxRuns];
   __shared__ uint32_t s_run_cnt[kMaxRuns];
   __shared__ unsigned long long s_surv, s_regs;
@@ -759,6 +771,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
       }
     }
     if (tid == 0) s_nspill = 0;
+    if (count_buckets && tid <= bmask) s_bcnt[tid] = 0;
 
     // tile t of the sequence is in buffer t & 1 (always buffer 0 without a
     // second buffer); tile 0 is issued here, tile t + 1 once tile t arrived
@@ -820,7 +833,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               } else if (spill_list) {
                 const int r = no_set ? 2 : sset_try_insert(sset, slog, slot, sprobes);
                 count_it = (r == 1);
-                if (r == 2) spill_push(spill_list, &s_nspill, slot);
+                if (r == 2) {
+                  spill_push(spill_list, &s_nspill, slot);
+                  if (count_buckets) atomicAdd(s_bcnt + ((slot >> 5) & bmask), 1u);
+                }
               } else {
                 count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
               }
@@ -903,7 +919,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
                 } else if (spill_list) {
                   const int r = no_set ? 2 : sset_try_insert(sset, slog, slot, sprobes);
                   count_it = (r == 1);
-                  if (r == 2) spill_push(spill_list, &s_nspill, slot);
+                  if (r == 2) {
+                  spill_push(spill_list, &s_nspill, slot);
+                  if (count_buckets) atomicAdd(s_bcnt + ((slot >> 5) & bmask), 1u);
+                }
                 } else {
                   count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
                 }
@@ -1093,7 +1112,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               } else if (spill_list) {
                 const int r = no_set ? 2 : sset_try_insert(sset, slog, slot, sprobes);
                 count_it = (r == 1);
-                if (r == 2) spill_push(spill_list, &s_nspill, slot);
+                if (r == 2) {
+                  spill_push(spill_list, &s_nspill, slot);
+                  if (count_buckets) atomicAdd(s_bcnt + ((slot >> 5) & bmask), 1u);
+                }
               } else {
                 count_it = seq_first_seen(sset, slog, gset, glog, epoch, slot, a.ctl);
               }
@@ -1136,7 +1158,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     if (stopped) break;  // uniform: every thread saw the same barrier result
     if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
       const uint32_t nsp = s_nspill;  // read after the tile loop's final barrier
-      if (nsp) dedupe_spills(a, lg, nsp, sset, tile0, a.tile_words + a.queue_words, spill_list, spill_part, my_regs);
+      if (nsp)
+        dedupe_spills(a, lg, nsp, sset, tile0, a.tile_words + a.queue_words, spill_list, spill_part, my_regs,
+                      count_buckets ? s_bcnt : nullptr, spill_kb);
       __syncthreads();
     }
   }
