@@ -271,7 +271,10 @@ ig_status intergrams_prefetch(ig_plan* pl, const void* host_data);
  *                              or the top-k after pass n) on the sums.
  * Every shard then holds the same P^(j) (the selection is deterministic), so
  * nothing else is exchanged; intergrams_topk gives the whole corpus's rows
- * on every shard. Calls are stream-ordered on the plan's stream; the export
+ * on every shard. A survivor list that runs out of room in a sharded pass is
+ * not grown and replayed (every shard would have to replay with it):
+ * intergrams_pass_select returns IG_ETABLE_FULL; give such plans a list_pct
+ * that holds the passes' candidates. Calls are stream-ordered on the plan's stream; the export
  * is complete once the stream has reached it, and the import must be
  * enqueued after the caller's reduction has written the buffer (synchronise
  * or order the streams). No counterpart in the paper, which runs on one
