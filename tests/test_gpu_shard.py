@@ -132,3 +132,57 @@ def test_checks_catch_a_planted_count():
         with pytest.raises(B.IntergramsError) as ei:
             pl.pass_select()
         assert ei.value.status == IG_ESTATE
+
+
+def test_split_pass_on_16_bit_counters_and_dna():
+    """The split pass (scan, export, import, select) on plans whose counters
+    are 16-bit (not sharded: exported widened to 32 bits, imported narrowed
+    back) and on 2-bit DNA with chain passes: the same rows as the plain
+    plan."""
+    cases = [(corpus(), dict(n=8, k=300, candidates=1200, base_n=3, symbol_bits=8)),
+             (synth.make_corpus("genomic_5gbp", m=4, max_len=40_000, seed=33)[:2],
+              dict(n=40, k=200, candidates=800, base_n=10, symbol_bits=2))]
+    for (data, off), p in cases:
+        d = torch.from_numpy(np.ascontiguousarray(data)).cuda()
+        o = torch.from_numpy(off.view(np.int64).copy()).cuda()
+        with B.Plan(d, o, **p) as pl:
+            pl.run()
+            ek, ec, _ = pl.topk()
+        for mode_flags in (dict(), dict(sharded=True, checks=True)):
+            with B.Plan(d, o, **p, **mode_flags) as pl:
+                while pl.pass_scan() is not None:
+                    buf = torch.empty(pl.counts_slots(), dtype=torch.int32, device="cuda")
+                    pl.counts_export(buf)
+                    pl.counts_import(buf.clone())
+                    pl.pass_select()
+                gk, gc, _ = pl.topk()
+            assert np.array_equal(gk, ek) and np.array_equal(gc, ec), (p, mode_flags)
+
+
+def test_split_pass_calls_out_of_order_are_refused():
+    data, off = corpus()
+    d = torch.from_numpy(data).cuda()
+    o = torch.from_numpy(off.view(np.int64)).cuda()
+    buf = torch.empty(1 << 24, dtype=torch.int32, device="cuda")
+    with B.Plan(d, o, n=5, k=100, candidates=400, base_n=3) as pl:
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.counts_export(buf)
+        assert ei.value.status == IG_ESTATE
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.pass_select()
+        assert ei.value.status == IG_ESTATE
+        pl.pass_scan()
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.pass_scan()                       # the first scan waits for its selection
+        assert ei.value.status == IG_ESTATE
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.step()                            # so does a whole pass
+        assert ei.value.status == IG_ESTATE
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.counts_import(buf[:5])            # wrong length
+        assert ei.value.status == -1
+        pl.pass_select()
+    with B.Plan(d, o, n=5, k=100, candidates=400, base_n=3, graph=True) as pl:
+        with pytest.raises(B.IntergramsError) as ei:
+            pl.pass_scan()                       # graph plans run whole jobs
+        assert ei.value.status == IG_ESTATE
