@@ -435,7 +435,7 @@ def main(argv=None):
     # end to end through the C ABI with host buffers: H2D of the corpus, every
     # pass, D2H of the top-k, inside the timed region; each step's corpus copy
     # is started (intergrams_prefetch) while the step before it runs
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(5, args.steps))
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(10, args.steps))
     hplan = binding.Plan(host.numpy()[:nbytes], off, **p, graph=True, host_input=True, stream=stream,
                          autotune=not args.no_autotune, tuning=tuning)  # the knobs the device plan got (cached)
     hplan.run()
