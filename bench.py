@@ -290,16 +290,18 @@ def serving_leg(args, seed):
     """Poisson job stream (config 5: jobs at 20/s over corpora of the 2 MiB
     workload's byte law, total sizes lognormal with median 64 MB, clamped to
     [1 MB, 2 GB]; n in {4, 8, 16}; k in {1K, 16K, 256K}; Z = 4k) through the
-    continuous-batching server (least work first, stream priorities by work),
-    and the same stream one job per launch in arrival order. Each job takes a
-    corpus from a pool of device-resident corpora drawn from the size law.
-    The same job mix at four times the rate is a second, shorter stream."""
+    continuous-batching server (oldest job first on the highest-priority
+    stream, jobs of 2 GB or more streamed running alone), and the same stream
+    one job per launch in arrival order. Each job takes a corpus from a pool of
+    device-resident corpora drawn from the size law. The same job mix at four
+    times the rate is a second, shorter stream."""
     import numpy as np
     from paper_2511_14955_gb300 import serving
     pool = serving.make_pool(args.serve_corpora, seed=seed + 7, hi_bytes=int(args.serve_max_gb * (1 << 30)))
     jobs = serving.job_stream(args.serve_jobs, args.serve_rate, len(pool), seed=seed + 11)
     tun = {"list_pct": 50}
-    batched = serving.run_stream(pool, jobs, max_active=8, tuning=tun)
+    policy = "oldest_first+large_alone"
+    batched = serving.run_stream(pool, jobs, max_active=8, tuning=tun, policy=policy)
     single = serving.run_stream(pool, jobs, max_active=1, tuning=tun, fifo=True)
     sizes = np.array([int(o[-1]) for _, o in pool])
     out = {"workload": f"{len(jobs)} Poisson jobs at {args.serve_rate:g}/s over {len(pool)} corpora "
@@ -308,7 +310,8 @@ def serving_leg(args, seed):
            "continuous_batching": batched, "one_job_per_launch": single}
     hot = serving.job_stream(args.serve_jobs_4x, 4 * args.serve_rate, len(pool), seed=seed + 11)
     out["at_4x_rate"] = {"rate_per_s": 4 * args.serve_rate, "jobs": len(hot),
-                         "continuous_batching": serving.run_stream(pool, hot, max_active=8, tuning=tun),
+                         "continuous_batching": serving.run_stream(pool, hot, max_active=8, tuning=tun,
+                                                                   policy=policy),
                          "one_job_per_launch": serving.run_stream(pool, hot, max_active=1, tuning=tun, fifo=True)}
     del pool
     return out

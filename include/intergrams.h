@@ -459,6 +459,8 @@ typedef struct {
   uint64_t mem_budget;   /* device bytes all active jobs' tables may use (0 = 80% of free memory) */
   uint32_t max_active;   /* jobs in flight at once (0 = 8) */
   uint32_t flags;        /* IG_SRV_* */
+  uint64_t large_work;   /* IG_SRV_LARGE_ALONE: a job is large from this many bytes streamed over
+                            all its passes (0 = 2e9, about 15 ms of scans on a GB300) */
 } ig_server_config;
 /* Server policy flags. Default (0): admit the pending job with the least
  * estimated work first (corpus bytes x passes plus its counter arrays; the
@@ -471,6 +473,12 @@ typedef struct {
  * level below the jobs already running when it was admitted, so the oldest
  * job's passes start first and younger jobs fill the gaps it leaves. */
 #define IG_SRV_OLDEST_FIRST (1u << 1)
+/* IG_SRV_LARGE_ALONE: a job whose estimated work is at least large_work
+ * bytes streamed (default 2 GB) is admitted only when no other job is
+ * running and runs with none beside it, so the largest jobs keep the whole
+ * GPU (a scan holds its SMs for a whole pass and is not preempted); smaller
+ * jobs still run together. Combines with the admission orders above. */
+#define IG_SRV_LARGE_ALONE (1u << 2)
 typedef struct {
   uint64_t submitted, completed, failed;
   uint32_t active, peak_active, pending;

@@ -26,6 +26,7 @@ F_TIMING = 1 << 3
 F_SHARDED = 1 << 7
 SRV_FIFO = 1 << 0
 SRV_OLDEST_FIRST = 1 << 1
+SRV_LARGE_ALONE = 1 << 2
 F_EXHAUSTIVE_CHECKS = 1 << 8
 
 # every symbol include/intergrams.h declares
@@ -59,7 +60,8 @@ class IgPassStats(ctypes.Structure):
 
 
 class IgServerConfig(ctypes.Structure):
-    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_active", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_active", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("large_work", ctypes.c_uint64)]
 
 
 class IgServerStats(ctypes.Structure):
@@ -395,13 +397,17 @@ class Server:
     """Continuous-batching job server (intergrams_server_*): submit jobs whose
     corpora are CUDA tensors, wait for their top-k. Marshalling only."""
 
-    def __init__(self, mem_budget: int = 0, max_active: int = 8, fifo: bool = False, policy: str | None = None):
-        """policy: "least_work_first" (default), "oldest_first" or "fifo"."""
+    def __init__(self, mem_budget: int = 0, max_active: int = 8, fifo: bool = False, policy: str | None = None,
+                 large_work: int = 0):
+        """policy: "least_work_first" (default), "oldest_first", "fifo", or
+        either of the first two with "+large_alone"."""
         self._lib = load()
         self._h = ctypes.c_void_p(None)
         policy = policy or ("fifo" if fifo else "least_work_first")
-        flags = {"least_work_first": 0, "oldest_first": SRV_OLDEST_FIRST, "fifo": SRV_FIFO}[policy]
-        cfg = IgServerConfig(int(mem_budget), int(max_active), flags)
+        flags = {"least_work_first": 0, "oldest_first": SRV_OLDEST_FIRST, "fifo": SRV_FIFO,
+                 "least_work_first+large_alone": SRV_LARGE_ALONE,
+                 "oldest_first+large_alone": SRV_OLDEST_FIRST | SRV_LARGE_ALONE}[policy]
+        cfg = IgServerConfig(int(mem_budget), int(max_active), flags, int(large_work))
         _check(self._lib, self._lib.intergrams_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "intergrams_server_create")
         self._keep = {}

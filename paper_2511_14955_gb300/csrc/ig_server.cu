@@ -48,6 +48,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// IG_SRV_LARGE_ALONE default: jobs that stream at least this many bytes over
+// all their passes (about 15 ms of scans on a GB300) run alone
+constexpr double kLargeWork = 2e9;
+
 enum JobState { kPending = 0, kPasses = 1, kTopk = 2, kDone = 3 };
 
 struct Job {
@@ -61,6 +65,7 @@ struct Job {
   uint64_t bytes = 0;  // device bytes charged against the budget
   double work = 0;     // estimated work: bytes streamed over all passes
   uint32_t behind = 0; // jobs already running when it was admitted
+  bool large = false;  // IG_SRV_LARGE_ALONE: runs with no other job beside it
   ig_plan* plan = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
@@ -92,6 +97,7 @@ struct ig_server {
   uint64_t next_id = 1;
   bool stop = false;
   uint32_t active = 0, peak_active = 0;
+  uint32_t large_active = 0;  // a large job is running alone
   uint64_t mem_used = 0, peak_mem = 0, submitted = 0, completed = 0, failed = 0;
   std::thread worker;
 };
@@ -153,6 +159,7 @@ void finish_job(ig_server* sv, Job* jb, ig_status st, const std::string& err) {
   jb->t_done = done;
   sv->mem_used -= jb->bytes;
   sv->active -= 1;
+  if (jb->large) sv->large_active -= 1;
   if (st == IG_OK) sv->completed += 1;
   else sv->failed += 1;
   sv->cv_done.notify_all();
@@ -210,7 +217,7 @@ void scheduler(ig_server* sv) {
       // admission while a slot is free and the budget allows: arrival order
       // (IG_SRV_FIFO), else the least work first, each job's work discounted
       // by its wait (it halves for every 100 ms waited, so none starves)
-      while (!sv->pending.empty() && sv->active < sv->cfg.max_active) {
+      while (!sv->pending.empty() && sv->active < sv->cfg.max_active && sv->large_active == 0) {
         auto pick = sv->pending.begin();
         if (!(sv->cfg.flags & (IG_SRV_FIFO | IG_SRV_OLDEST_FIRST))) {
           const Clock::time_point now = Clock::now();
@@ -226,6 +233,12 @@ void scheduler(ig_server* sv) {
         }
         Job* jb = *pick;
         if (sv->mem_used + jb->bytes > sv->cfg.mem_budget && sv->active > 0) break;
+        // a large job waits for the GPU to drain, then runs alone (the jobs
+        // picked after it wait with it, so it cannot starve)
+        jb->large = (sv->cfg.flags & IG_SRV_LARGE_ALONE) &&
+                    jb->work >= (sv->cfg.large_work ? (double)sv->cfg.large_work : kLargeWork);
+        if (jb->large && sv->active > 0) break;
+        if (jb->large) sv->large_active += 1;
         sv->pending.erase(pick);
         sv->mem_used += jb->bytes;
         sv->peak_mem = std::max(sv->peak_mem, sv->mem_used);

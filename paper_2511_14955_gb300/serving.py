@@ -62,7 +62,7 @@ def job_stream(n_jobs: int, rate: float, n_corpora: int, seed: int, ns=(4, 8, 16
 
 def run_stream(pool, jobs, *, max_active: int, mem_budget: int = 0, z_factor: int = 4, base_n: int = 3,
                tuning: dict | None = None, keep_results: bool = False, fifo: bool = False,
-               policy: str | None = None):
+               policy: str | None = None, large_work: int = 0):
     """Submit every job at its arrival time; returns latency and throughput
     figures. ``policy``: "least_work_first" (the server's default),
     "oldest_first" or "fifo" (arrival order on default-priority streams, the
@@ -70,7 +70,7 @@ def run_stream(pool, jobs, *, max_active: int, mem_budget: int = 0, z_factor: in
     results = {}
     lat = [None] * len(jobs)
     policy = policy or ("fifo" if fifo else "least_work_first")
-    with binding.Server(mem_budget=mem_budget, max_active=max_active, policy=policy) as sv:
+    with binding.Server(mem_budget=mem_budget, max_active=max_active, policy=policy, large_work=large_work) as sv:
         ids = [None] * len(jobs)
         ready = threading.Event()
         errors = []

@@ -117,3 +117,20 @@ def test_served_job_grows_its_survivor_lists(pool):
         jid = sv.submit(data, off, n=8, k=256, candidates=1024, base_n=3, tuning=dict(chain_from=5, list_pct=1))
         keys, counts, _ = sv.wait(jid, timeout_s=120)
     assert np.array_equal(counts, want[1]) and np.array_equal(keys, want[0])
+
+
+def test_large_jobs_run_alone(pool):
+    """IG_SRV_LARGE_ALONE with every job counted as large (a 1-byte
+    threshold): no two jobs ever run together, under either admission order,
+    and every result is exact."""
+    jobs = serving.job_stream(10, rate=2000.0, n_corpora=len(pool), seed=17, ns=(4, 8), ks=(64, 512))
+    for policy in ("oldest_first+large_alone", "least_work_first+large_alone"):
+        summary, results = serving.run_stream(pool, jobs, max_active=8, policy=policy, large_work=1,
+                                              keep_results=True)
+        assert summary["peak_active"] == 1
+        for i, jb in enumerate(jobs):
+            ek, ec = alone(pool, jb)
+            assert np.array_equal(results[i][1], ec) and np.array_equal(results[i][0], ek)
+    # with the default threshold these small jobs overlap
+    summary = serving.run_stream(pool, jobs, max_active=8, policy="oldest_first+large_alone")
+    assert summary["peak_active"] >= 2
