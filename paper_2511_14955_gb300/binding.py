@@ -50,7 +50,7 @@ class IgTuning(ctypes.Structure):
                 ("ctas_per_sm", "threads", "words_per_thread", "smem_set_log2", "table_load_pct", "hot_log2",
                  "chain_from", "list_pct", "log_mode", "log_pct", "log_chunk_log2", "log_range_log2",
                  "dedupe_bitmap", "dense_prefix", "base_words_per_thread", "base_smem_set_log2",
-                 "set_probes", "tile_buffers", "rs_depth", "tile_cache_hint", "prefetch_tiles", "spill_dedupe", "spill_min_fill", "carry_slots", "set_max_windows")]
+                 "set_probes", "tile_buffers", "rs_depth", "tile_cache_hint", "prefetch_tiles", "spill_dedupe", "spill_min_fill", "carry_slots", "set_max_windows", "scan_variants")]
 
 
 class IgPassStats(ctypes.Structure):

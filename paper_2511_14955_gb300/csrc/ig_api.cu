@@ -388,6 +388,7 @@ uint32_t enqueue_scan(ig_plan* pl, uint32_t j, cudaStream_t s) {
   a.range_dedupe = pl->t.spill_dedupe != 1u;
   a.range_min_fill = pl->t.spill_min_fill ? pl->t.spill_min_fill - 1u : 512u;
   a.set_max_windows = pl->t.set_max_windows;
+  a.general_only = pl->t.scan_variants == 1;
   if (base) {  // the base pass's own tile and set; no queue
     a.words_per_thread = pl->base_wpt;
     a.sset_log2 = pl->base_sset_log2;
@@ -786,7 +787,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
   if (t.ctas_per_sm > 4 || (t.threads != 256 && t.threads != 512 && t.threads != 1024) ||
       !(t.words_per_thread & 1u) || t.words_per_thread > 31 || t.smem_set_log2 < 8 || t.smem_set_log2 > 15 ||
       t.table_load_pct < 10 || t.table_load_pct > 50 || t.hot_log2 < 6 || t.hot_log2 > 13 || t.list_pct > 200 ||
-      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.tile_cache_hint > 2 || t.prefetch_tiles > 9 || t.spill_dedupe > 2 || t.carry_slots > 2 || t.set_probes > 8 || t.tile_buffers > 2 || t.dense_prefix > 4 || t.rs_depth > kMaxRsLevels || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
+      t.log_mode > 1 || t.dedupe_bitmap > 2 || t.tile_cache_hint > 2 || t.prefetch_tiles > 9 || t.spill_dedupe > 2 || t.carry_slots > 2 || t.scan_variants > 2 || t.set_probes > 8 || t.tile_buffers > 2 || t.dense_prefix > 4 || t.rs_depth > kMaxRsLevels || t.log_pct > 400 || (t.log_chunk_log2 && (t.log_chunk_log2 < 14 || t.log_chunk_log2 > 20)) ||
       (t.log_range_log2 && (t.log_range_log2 < 10 || t.log_range_log2 > 30)))
     return bail(fail(IG_EINVAL, "tuning knob out of range"));
   pl->t = t;

@@ -148,6 +148,7 @@ struct ScanArgs {
   uint32_t range_dedupe;       // Eq. 2 spill dedupe by word bucket and bit vector (else hash partition + set)
   uint32_t range_min_fill;     // ... for sequences whose spills fill each bucket with at least this many
   uint32_t set_max_windows;    // Eq. 2: sequences with more windows skip the shared-memory set (0 = never)
+  uint32_t general_only;       // never launch a configuration's compiled variant
   PassCtl* ctl;
 };
 

@@ -338,8 +338,10 @@ __device__ __forceinline__ uint32_t spill_bucket(uint32_t x, uint32_t shift, uin
   return kb == 0 ? 0u : (x << shift) >> (32 - kb);
 }
 
+// FIX: 16-bit counters known at compile time.
+template <bool FIX = false>
 __device__ __forceinline__ void count_at_once(const ScanArgs& a, uint32_t slot) {
-  if (a.narrow) {  // 16-bit counter slot of word slot / 2 (little-endian half); counts < 65536
+  if (FIX || a.narrow) {  // 16-bit counter slot of word slot / 2 (little-endian half); counts < 65536
     atomicAdd(a.counts + (slot >> 1), 1u << ((slot & 1u) << 4));
     return;
   }
@@ -367,8 +369,9 @@ __device__ __forceinline__ void log_init(const LogState& lg) {
 // Count `slot` (Eq. 1 / Eq. 2 increment of C): appended to the log when the
 // pass keeps one, else counted at once. A chunk that is somehow full also
 // falls back to counting at once, so the log never overflows.
+template <bool FIX = false>
 __device__ __forceinline__ void register_slot(const ScanArgs& a, const LogState& lg, uint32_t slot) {
-  if (a.rlog) {
+  if (!FIX && a.rlog) {
     const uint32_t r = slot >> a.range_shift;
     const uint32_t c = lg.chunk[r];
     if (c < kNoChunk) {
@@ -384,7 +387,7 @@ __device__ __forceinline__ void register_slot(const ScanArgs& a, const LogState&
       }
     }
   }
-  count_at_once(a, slot);
+  count_at_once<FIX>(a, slot);
 }
 
 // Before a step that registers at most `need` slots (threads < nranges; the
@@ -453,7 +456,8 @@ constexpr uint32_t kDead = 0xFFFFFFFDu;  // rank/select chain: a level's bit was
 // shared-memory set, sized to at least twice the entries (at most the whole
 // set); each distinct slot is registered once. Fits whenever hi - lo <=
 // capacity / 2.
-__device__ void insert_range(const ScanArgs& a, const LogState& lg, const uint32_t* src, uint32_t lo, uint32_t hi,
+template <bool FIX = false>
+__device__ __forceinline__ void insert_range(const ScanArgs& a, const LogState& lg, const uint32_t* src, uint32_t lo, uint32_t hi,
                              uint32_t* sset, unsigned long long& my_regs) {
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
   uint32_t slog = ceil_log2_u64(2ull * (hi - lo));
@@ -471,7 +475,7 @@ __device__ void insert_range(const ScanArgs& a, const LogState& lg, const uint32
     for (uint32_t k = 0; k < kBatch; ++k) {
       if (i0 + k * nthr < hi && sset_insert_full(sset, slog, v[k], a.ctl)) {
         ++my_regs;
-        register_slot(a, lg, v[k]);
+        register_slot<FIX>(a, lg, v[k]);
       }
     }
   }
@@ -581,7 +585,8 @@ __device__ void partition_by_word(const uint32_t* src, uint32_t* dst, uint32_t l
 // the thread that sets a slot's bit registers it. The bits are cleared again
 // word by word after use, or all at once when the bucket holds more entries
 // than the vector has words.
-__device__ void bitmap_bucket(const ScanArgs& a, const LogState& lg, const uint32_t* src, uint32_t lo, uint32_t hi,
+template <bool FIX = false>
+__device__ __forceinline__ void bitmap_bucket(const ScanArgs& a, const LogState& lg, const uint32_t* src, uint32_t lo, uint32_t hi,
                               uint32_t kb, uint32_t* bm, uint32_t bm_words, unsigned long long& my_regs) {
   const uint32_t tid = threadIdx.x, nthr = blockDim.x, ws = 5u + kb;
   if (a.rlog) {
@@ -598,7 +603,7 @@ __device__ void bitmap_bucket(const ScanArgs& a, const LogState& lg, const uint3
         const uint32_t bit = 1u << (v[k] & 31u);
         if (!(atomicOr(bm + (v[k] >> ws), bit) & bit)) {
           ++my_regs;
-          register_slot(a, lg, v[k]);
+          register_slot<FIX>(a, lg, v[k]);
         }
       }
     }
@@ -618,7 +623,8 @@ __device__ void bitmap_bucket(const ScanArgs& a, const LogState& lg, const uint3
 // large enough that a bucket's slots fit one bit vector in the set's shared
 // memory, and each bucket is deduplicated with that bit vector. One
 // partition level, no hashing, no probing.
-__device__ void dedupe_spills_by_word(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t kb, uint32_t* sset,
+template <bool FIX = false>
+__device__ __forceinline__ void dedupe_spills_by_word(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t kb, uint32_t* sset,
                                       uint32_t* scratch, uint32_t* list, uint32_t* part, const uint32_t* counts,
                                       unsigned long long& my_regs) {
   const uint32_t words = 1u << a.sset_log2, K = 1u << kb;
@@ -626,7 +632,7 @@ __device__ void dedupe_spills_by_word(const ScanArgs& a, const LogState& lg, uin
   partition_by_word(list, part, 0, S, kb, scratch, scratch + K + 1, counts);
   for (uint32_t b = 0; b < K; ++b) {
     const uint32_t lo = scratch[b], hi = scratch[b + 1];
-    if (hi > lo) bitmap_bucket(a, lg, part, lo, hi, kb, sset, words, my_regs);  // uniform across the CTA
+    if (hi > lo) bitmap_bucket<FIX>(a, lg, part, lo, hi, kb, sset, words, my_regs);  // uniform across the CTA
   }
 }
 
@@ -634,13 +640,14 @@ __device__ void dedupe_spills_by_word(const ScanArgs& a, const LogState& lg, uin
 // included, disjoint from the slots already in the set) are hash-partitioned
 // (at most two levels, bucket tables in the free tile buffer) into buckets of
 // at most half the set's capacity, and each bucket is deduplicated exactly.
-__device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t* sset, uint32_t* scratch,
+template <bool FIX = false>
+__device__ __forceinline__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S, uint32_t* sset, uint32_t* scratch,
                               uint32_t scratch_words, uint32_t* list, uint32_t* part,
                               unsigned long long& my_regs, const uint32_t* bucket_counts = nullptr,
                               uint32_t counted_kb = 0xFFFFFFFFu) {
   const uint32_t cap = 1u << a.sset_log2, fit = cap / 2;
   if (S <= fit) {
-    insert_range(a, lg, list, 0, S, sset, my_regs);
+    insert_range<FIX>(a, lg, list, 0, S, sset, my_regs);
     return;
   }
   if (a.range_dedupe && a.nslots) {
@@ -649,7 +656,7 @@ __device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S,
     while ((a.nslots + 31) / 32 > ((uint64_t)cap << kb)) ++kb;
     // worth its two barriers per bucket once the buckets are well filled
     if (2 * (1ull << kb) + 1 <= scratch_words && ((uint64_t)S >> kb) >= a.range_min_fill) {
-      dedupe_spills_by_word(a, lg, S, kb, sset, scratch, list, part, kb == counted_kb ? bucket_counts : nullptr,
+      dedupe_spills_by_word<FIX>(a, lg, S, kb, sset, scratch, list, part, kb == counted_kb ? bucket_counts : nullptr,
                             my_regs);
       return;
     }
@@ -667,7 +674,7 @@ __device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S,
     const uint32_t lo = bnd1[b1], hi = bnd1[b1 + 1];
     if (hi == lo) continue;  // uniform across the CTA
     if (hi - lo <= fit) {
-      insert_range(a, lg, part, lo, hi, sset, my_regs);
+      insert_range<FIX>(a, lg, part, lo, hi, sset, my_regs);
       continue;
     }
     const uint32_t kb2 = bucket_bits(hi - lo, cap, kbmax);
@@ -675,13 +682,30 @@ __device__ void dedupe_spills(const ScanArgs& a, const LogState& lg, uint32_t S,
     partition_range(part, list, lo, hi, kb1, kb2, bnd2, bnd2 + K2 + 1);
     for (uint32_t b2 = 0; b2 < K2; ++b2) {
       const uint32_t l2 = bnd2[b2], h2 = bnd2[b2 + 1];
-      if (h2 > l2) insert_range(a, lg, list, l2, h2, sset, my_regs);
+      if (h2 > l2) insert_range<FIX>(a, lg, list, l2, h2, sset, my_regs);
     }
   }
 }
 
-template <int SB, bool BASE>
-__global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
+// RS = 0: every switch of ScanArgs read at run time; RS = 1 or 2: the
+// configuration of the rank/select passes (RS levels, Eq. 2 with the set and
+// spill lists, 16-bit counters; no carried slots, hot cache, dense map,
+// window runs, survivor lists, registration log, bit vectors or global sets)
+// fixed at compile time.
+template <int SB, bool BASE, uint32_t RS>
+__device__ __forceinline__ void scan_body(const ScanArgs& a) {
+  constexpr bool kFix = RS != 0;
+  const uint32_t rs_depth = kFix ? RS : a.rs_depth;
+  const uint32_t carry_in = kFix ? 0u : a.carry_in, carry_out = kFix ? 0u : a.carry_out;
+  uint32_t* const carry = kFix ? nullptr : a.carry;
+  const uint32_t hot_log2 = kFix ? 0u : a.hot_log2;
+  const uint32_t* const dmap = kFix ? nullptr : a.dmap;
+  const uint32_t first_runs = kFix ? 0u : a.first_runs;
+  unsigned long long* const list_out = kFix ? nullptr : a.list_out;
+  const bool seq_mode = kFix || a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE;
+  const uint32_t set_max_windows = kFix ? 0u : a.set_max_windows;
+  const uint32_t prefetch_tiles = kFix ? 0u : a.prefetch_tiles;
+  uint32_t* const rlog = kFix ? nullptr : a.rlog;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_item, s_nspill, s_qn;
   // spills per bit-vector bucket of the sequence, counted as they are
@@ -703,7 +727,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
   const uint32_t R = a.words_per_thread * S::kPerWord;  // windows per thread per tile
   const uint32_t tile_windows = R * nthr;
-  const uint32_t H = (BASE || a.hot_log2 == 0) ? 0u : (1u << a.hot_log2);
+  const uint32_t H = (BASE || hot_log2 == 0) ? 0u : (1u << hot_log2);
   // shared memory: [dedupe set][hot keys][hot ids][tile]
   uint32_t* sset = smem;
   unsigned long long* hot_keys = reinterpret_cast<unsigned long long*>(smem + (1u << a.sset_log2));
@@ -722,8 +746,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   }
   uint32_t bar_phases = 0;  // bit b: phase parity of barrier b
   const uint32_t alive_tile_words = (tile_windows + 31) / 32;
-  unsigned long long* gset = a.gset ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
-  uint32_t* bm = a.bitmap ? a.bitmap + (uint64_t)blockIdx.x * a.bitmap_words : nullptr;
+  unsigned long long* gset = (!kFix && a.gset) ? a.gset + ((unsigned long long)blockIdx.x << a.gset_log2) : nullptr;
+  uint32_t* bm = (!kFix && a.bitmap) ? a.bitmap + (uint64_t)blockIdx.x * a.bitmap_words : nullptr;
   // CTA-private spill list and partition buffer (Eq. 2 without a global set)
   uint32_t* spill_list = a.spill ? a.spill + (uint64_t)blockIdx.x * 2 * a.spill_cap : nullptr;
   uint32_t* spill_part = spill_list ? spill_list + a.spill_cap : nullptr;
@@ -756,9 +780,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     const uint32_t sprobes = a.set_probes;
     // a sequence this long sends every survivor straight to its spill list
     // (the set would only hold a small share of its slots)
-    const bool no_set = a.set_max_windows && W > a.set_max_windows;
+    const bool no_set = set_max_windows && W > set_max_windows;
     uint32_t slog = 0, glog = 0;
-    if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+    if (seq_mode) {
       uint32_t need = ceil_log2_u64(2 * W);
       slog = need < a.sset_log2 ? need : a.sset_log2;
       if (slog < 1) slog = 1;
@@ -777,7 +801,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
     // second buffer); tile 0 is issued here, tile t + 1 once tile t arrived
     __syncthreads();  // the previous sequence is done with both buffers
     stage_issue(a, tile_geom<SB>(a, s0, W, 0, tile_windows, j), reinterpret_cast<uint8_t*>(tile0), &s_bar[0]);
-    for (uint32_t d = 1; d <= a.prefetch_tiles; ++d)
+    for (uint32_t d = 1; d <= prefetch_tiles; ++d)
       if ((uint64_t)d * tile_windows < W) prefetch_tile(a, tile_geom<SB>(a, s0, W, (uint64_t)d * tile_windows, tile_windows, j));
     uint32_t tix = 0;
     for (uint64_t w0 = 0; w0 < W; w0 += tile_windows, ++tix) {
@@ -803,8 +827,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
       if (a.tile2 && w0 + tile_windows < W)
         stage_issue(a, tile_geom<SB>(a, s0, W, w0 + tile_windows, tile_windows, j),
                     reinterpret_cast<uint8_t*>(bsel ? tile0 : tile1), s_bar + (bsel ^ 1u));
-      if (a.prefetch_tiles && w0 + (uint64_t)(a.prefetch_tiles + 1) * tile_windows < W)
-        prefetch_tile(a, tile_geom<SB>(a, s0, W, w0 + (uint64_t)(a.prefetch_tiles + 1) * tile_windows, tile_windows, j));
+      if (prefetch_tiles && w0 + (uint64_t)(prefetch_tiles + 1) * tile_windows < W)
+        prefetch_tile(a, tile_geom<SB>(a, s0, W, w0 + (uint64_t)(prefetch_tiles + 1) * tile_windows, tile_windows, j));
 
       const uint32_t wb = tid * R;
       if (BASE) {
@@ -827,7 +851,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             const uint32_t slot = (uint32_t)key;
             ++my_surv;
             bool count_it = true;
-            if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+            if (seq_mode) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
@@ -843,11 +867,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             }
             if (count_it) {
               ++my_regs;
-              count_at_once(a, slot);  // the dense base pass never keeps a log
+              count_at_once<kFix>(a, slot);  // the dense base pass never keeps a log
             }
           }
         }
-      } else if (a.first_runs) {
+      } else if (first_runs) {
         // first candidate pass: every window is a candidate, so each thread
         // rolls the key over its own run of windows as in the base pass; the
         // (j-1)-gram prefix indexes the dense map, or goes to the hot cache
@@ -890,11 +914,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
                 key = ((key << SB) | sym) & kmask;
                 kk[k] = key;
                 const uint32_t prefix = key >> SB;
-                if (a.dmap) {
-                  rk[k] = __ldg(a.dmap + prefix);
+                if (dmap) {
+                  rk[k] = __ldg(dmap + prefix);
                 } else {
                   if (H) {
-                    const uint32_t h = hash64_top(prefix, a.hot_log2);
+                    const uint32_t h = hash64_top(prefix, hot_log2);
                     if (hot_keys[h] == prefix) rk[k] = hot_ids[h];
                   }
                   if (rk[k] == kEmpty32) {
@@ -913,7 +937,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               if (a.alive_out) atomicOr(tile_alive + (wt >> 5), 1u << (wt & 31));
               ++my_surv;
               bool count_it = true;
-              if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+              if (seq_mode) {
                 if (bm) {
                   count_it = bitmap_first(bm, slot);
                 } else if (spill_list) {
@@ -929,7 +953,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
               }
               if (count_it) {
                 ++my_regs;
-                register_slot(a, lg, slot);
+                register_slot<kFix>(a, lg, slot);
               }
             }
           }
@@ -1002,7 +1026,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
         const uint32_t qn = s_qn;
         const uint32_t tile_g = a.tile_base[seq] + (uint32_t)(w0 / a.tile_windows);
         const uint32_t nruns = (qn + kRunChunk - 1) / kRunChunk;
-        if (a.list_out) {
+        if (list_out) {
           if (tid < nruns) {
             const uint32_t rn = (qn - tid * kRunChunk) < kRunChunk ? qn - tid * kRunChunk : kRunChunk;
             unsigned long long base = atomicAdd(&a.ctl->list_used, (unsigned long long)rn);
@@ -1018,10 +1042,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
         }
         // phase B: probe, count, dedupe the queued windows (in steps of at
         // most chunk / 8 when registrations go to the log)
-        const uint32_t step = a.rlog ? (1u << a.rlog_chunk_log2) >> 3 : (qn ? qn : 1u);
+        const uint32_t step = rlog ? (1u << a.rlog_chunk_log2) >> 3 : (qn ? qn : 1u);
         for (uint32_t q0 = 0; q0 < qn; q0 += step) {
         const uint32_t q1 = qn - q0 < step ? qn : q0 + step;
-        if (a.rlog) {
+        if (rlog) {
           log_room(a, lg, q1 - q0);
           __syncthreads();
         }
@@ -1043,11 +1067,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             if (qi < q1) {
               const uint32_t w = queue[qi];
               wl[k] = (w << 8) | tile_sym<SB>(tile, sym_off + w + j - 1);
-              if (a.rs_depth && a.carry_in) {  // the last level: the window's slot in the previous pass
-                prefix[k] = a.carry[gsym + w];
-                const uint2 pe = __ldg(a.rs[a.rs_depth - 1] + (prefix[k] >> 5));
+              if (rs_depth && carry_in) {  // the last level: the window's slot in the previous pass
+                prefix[k] = carry[gsym + w];
+                const uint2 pe = __ldg(a.rs[rs_depth - 1] + (prefix[k] >> 5));
                 e[k] = make_uint4(pe.x, pe.y, 0, 0);
-              } else if (a.rs_depth) {  // level 0: the base-length prefix; its word and the count before it
+              } else if (rs_depth) {  // level 0: the base-length prefix; its word and the count before it
                 prefix[k] = tile_key32<SB>(tile, sym_off + w, a.base_len);
                 const uint2 pe = __ldg(a.rs[0] + (prefix[k] >> 5));
                 e[k] = make_uint4(pe.x, pe.y, 0, 0);
@@ -1055,26 +1079,29 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
                 prefix[k] = short_key ? tile_key32<SB>(tile, sym_off + w, j - 1) : tile_key<SB>(tile, sym_off + w, j - 1);
                 hp = prefix[k] * 0x9E3779B97F4A7C15ull;
                 if (H) {
-                  const uint32_t h = (uint32_t)(hp >> (64 - a.hot_log2));
+                  const uint32_t h = (uint32_t)(hp >> (64 - hot_log2));
                   if (hot_keys[h] == prefix[k]) id[k] = hot_ids[h];
                 }
                 if (id[k] == kEmpty32) e[k] = __ldg(a.table + (uint32_t)(hp >> (64 - a.table_log2)));
               }
             }
           }
-          if (a.rs_depth) {
+          if (rs_depth) {
             // rank/select chain: the byte-order id of the prefix's first
             // base_len + L symbols at level L is its position among the
             // selected slots of pass base + L (all levels' loads of a round
             // are issued together)
-            for (uint32_t L = a.carry_in ? a.rs_depth - 1 : 0;; ++L) {
+            const uint32_t L0 = carry_in ? rs_depth - 1 : 0;
+#pragma unroll
+            for (uint32_t L = 0; L < kMaxRsLevels; ++L) {  // levels L0 .. rs_depth - 1
+              if (L < L0) continue;
 #pragma unroll
               for (uint32_t k = 0; k < kProbeBatch; ++k) {
                 if (wl[k] == 0xFFFFFFFFu || id[k] == kDead) continue;
                 const uint32_t bit = (uint32_t)prefix[k] & 31u;
                 id[k] = ((e[k].x >> bit) & 1u) ? e[k].y + __popc(e[k].x & ((1u << bit) - 1u)) : kDead;
               }
-              if (L + 1 >= a.rs_depth) break;
+              if (L + 1 >= rs_depth) break;
 #pragma unroll
               for (uint32_t k = 0; k < kProbeBatch; ++k) {
                 if (wl[k] == 0xFFFFFFFFu || id[k] == kDead) continue;
@@ -1091,22 +1118,22 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
 #pragma unroll
           for (uint32_t k = 0; k < kProbeBatch; ++k) {
             if (wl[k] == 0xFFFFFFFFu) continue;
-            if (!a.rs_depth && id[k] == kEmpty32) id[k] = probe_from(a.table, a.table_log2, prefix[k], e[k], a.ctl);
+            if (!rs_depth && id[k] == kEmpty32) id[k] = probe_from(a.table, a.table_log2, prefix[k], e[k], a.ctl);
             if (id[k] == kEmpty32) continue;
             const uint32_t qi = qb + k * nthr;
             const uint32_t w = wl[k] >> 8, last = wl[k] & 255u;
             const uint32_t slot = (id[k] << SB) | last;
-            if (a.carry_out) a.carry[gsym + w] = slot;
+            if (carry_out) carry[gsym + w] = slot;
             if (a.alive_out) atomicOr(tile_alive + (w >> 5), 1u << (w & 31));
-            if (a.list_out) {
+            if (list_out) {
               const uint32_t r = qi / kRunChunk;
               if (s_run_base[r] != ~0ull)
-                a.list_out[s_run_base[r] + atomicAdd(s_run_cnt + r, 1u)] =
+                list_out[s_run_base[r] + atomicAdd(s_run_cnt + r, 1u)] =
                     ((unsigned long long)slot << 32) | (uint32_t)(w0 + w);
             }
             ++my_surv;
             bool count_it = true;
-            if (a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+            if (seq_mode) {
               if (bm) {
                 count_it = bitmap_first(bm, slot);
               } else if (spill_list) {
@@ -1122,13 +1149,13 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
             }
             if (count_it) {
               ++my_regs;
-              register_slot(a, lg, slot);
+              register_slot<kFix>(a, lg, slot);
             }
           }
         }
-        if (a.rlog) __syncthreads();
+        if (rlog) __syncthreads();
         }
-        if (a.list_out) {
+        if (list_out) {
           __syncthreads();
           if (tid < nruns) {
             const uint32_t run = tile_g * a.runs_per_tile + tid;
@@ -1156,10 +1183,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
                     reinterpret_cast<uint8_t*>(tile0), &s_bar[0]);
     }
     if (stopped) break;  // uniform: every thread saw the same barrier result
-    if (spill_list && a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE) {
+    if (spill_list && seq_mode) {
       const uint32_t nsp = s_nspill;  // read after the tile loop's final barrier
       if (nsp)
-        dedupe_spills(a, lg, nsp, sset, tile0, a.tile_words + a.queue_words, spill_list, spill_part, my_regs,
+        dedupe_spills<kFix>(a, lg, nsp, sset, tile0, a.tile_words + a.queue_words, spill_list, spill_part, my_regs,
                       count_buckets ? s_bcnt : nullptr, spill_kb);
       __syncthreads();
     }
@@ -1195,6 +1222,32 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
 // search finds an entry's run), and the chunk's survivors are written as one
 // run at the chunk's first index (the others stay empty). Only a few
 // barriers per chunk, however few survivors a tile has.
+template <int SB, bool BASE>
+__global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
+  scan_body<SB, BASE, 0>(a);
+}
+
+// The candidate scan of byte corpora in the configuration of the rank/select
+// passes - prefix ids by DEPTH rank/select levels, Eq. 2 with the set and
+// spill lists, 16-bit counters, survivors not listed - with the switches of
+// every other configuration fixed at compile time (the same code, fewer
+// branches and live values).
+template <uint32_t DEPTH>
+__global__ void __launch_bounds__(1024) scan_rs_kernel(const ScanArgs a) {
+  scan_body<8, false, DEPTH>(a);
+}
+
+// The depth of the scan_rs_kernel that stands in for scan_kernel with these
+// arguments (0 = none: the general kernel runs).
+uint32_t rs_variant(const ScanArgs& a, uint32_t symbol_bits, bool base_pass) {
+  if (a.general_only || symbol_bits != 8 || base_pass || a.rs_depth < 1 || a.rs_depth > 2 || a.carry ||
+      a.hot_log2 || a.dmap || a.first_runs || a.list_out || a.rlog || a.bitmap || a.gset || !a.narrow ||
+      a.check_overflow || a.count_mode != IG_COUNT_ONCE_PER_SEQUENCE || !a.spill || a.set_max_windows ||
+      a.prefetch_tiles)
+    return 0;
+  return a.rs_depth;
+}
+
 template <int SB>
 __global__ void __launch_bounds__(1024) chain_kernel(const ScanArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -1402,6 +1455,11 @@ void* pick(uint32_t symbol_bits, bool base_pass) {
 }  // namespace
 
 cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem) {
+  if (symbol_bits == 8 && !base_pass)
+    for (void* f : {reinterpret_cast<void*>(scan_rs_kernel<1>), reinterpret_cast<void*>(scan_rs_kernel<2>)}) {
+      const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
   return cudaFuncSetAttribute(pick(symbol_bits, base_pass), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
@@ -1439,7 +1497,10 @@ void launch_log_count(const ScanArgs& a, cudaStream_t s) {
 void launch_scan(const ScanArgs& a, uint32_t symbol_bits, bool base_pass, int grid, int threads,
                  size_t smem, cudaStream_t s) {
   if (symbol_bits == 8) {
-    if (base_pass) scan_kernel<8, true><<<grid, threads, smem, s>>>(a);
+    const uint32_t rs = rs_variant(a, symbol_bits, base_pass);
+    if (rs == 1) scan_rs_kernel<1><<<grid, threads, smem, s>>>(a);
+    else if (rs == 2) scan_rs_kernel<2><<<grid, threads, smem, s>>>(a);
+    else if (base_pass) scan_kernel<8, true><<<grid, threads, smem, s>>>(a);
     else scan_kernel<8, false><<<grid, threads, smem, s>>>(a);
   } else {
     if (base_pass) scan_kernel<2, true><<<grid, threads, smem, s>>>(a);

@@ -118,6 +118,8 @@ def test_dna_reduced(mode):
     dict(spill_min_fill=1, smem_set_log2=10),                                 # spills by bit vector, always
     dict(dense_prefix=4, rs_depth=3, carry_slots=2),                          # carried slots
     dict(chain_from=6),                                                       # no chain passes
+    dict(scan_variants=1, dedupe_bitmap=1),                                   # general kernel only
+    dict(dedupe_bitmap=1, rs_depth=1),                                        # one-level variant
 ])
 def test_results_do_not_depend_on_tuning(tuning):
     data, off, _ = synth.make_corpus("markov_2mb", seed=2)
