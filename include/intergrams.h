@@ -163,11 +163,11 @@ typedef struct {
   uint32_t set_max_windows;  /* Eq. 2: a sequence with more windows than this sends every survivor
                                 straight to its spill list, skipping the shared-memory set (0 =
                                 default: never) */
-  uint32_t scan_variants;    /* candidate scans in a configuration with a compiled variant of their
-                                own (rank/select prefixes over one or two levels, Eq. 2 with the set
-                                and spill lists, 16-bit counters) run that variant, with the other
-                                configurations' switches fixed at compile time: 2 = on, 1 = off (every
-                                scan runs the general kernel), 0 = default (on) */
+  uint32_t scan_variants;    /* byte-corpus scans under Eq. 2 with the set and spill lists and 16-bit
+                                counters (the base pass; candidate passes with rank/select prefixes
+                                over one or two levels, or with the probe table) run compiled variants
+                                with the other configurations' switches fixed at compile time: 2 = on,
+                                1 = off (every scan runs the general kernel), 0 = default (on) */
 } ig_tuning;
 
 typedef struct ig_plan ig_plan;

@@ -26,6 +26,8 @@
 //
 // chain_kernel runs a pass from the previous pass's survivor lists instead
 // of the corpus (keys longer than 64 bits).
+#include <vector>
+
 #include "ig_internal.cuh"
 
 namespace ig {
@@ -687,21 +689,21 @@ __device__ __forceinline__ void dedupe_spills(const ScanArgs& a, const LogState&
   }
 }
 
-// RS = 0: every switch of ScanArgs read at run time; RS = 1 or 2: the
-// configuration of the rank/select passes (RS levels, Eq. 2 with the set and
-// spill lists, 16-bit counters; no carried slots, hot cache, dense map,
-// window runs, survivor lists, registration log, bit vectors or global sets)
-// fixed at compile time.
-template <int SB, bool BASE, uint32_t RS>
+// V = 0: every switch of ScanArgs read at run time. V = 1..3: Eq. 2 with
+// the set and spill lists and 16-bit counters, without carried slots, dense
+// map, window runs, registration log, bit vectors or global sets, fixed at
+// compile time; V = 1 or 2: prefix ids by V rank/select levels (no hot cache,
+// survivors not listed); V = 3: the probe table (or the base pass).
+template <int SB, bool BASE, uint32_t V>
 __device__ __forceinline__ void scan_body(const ScanArgs& a) {
-  constexpr bool kFix = RS != 0;
-  const uint32_t rs_depth = kFix ? RS : a.rs_depth;
+  constexpr bool kFix = V != 0, kRs = V == 1 || V == 2;
+  const uint32_t rs_depth = kRs ? V : (V == 3 ? 0u : a.rs_depth);
   const uint32_t carry_in = kFix ? 0u : a.carry_in, carry_out = kFix ? 0u : a.carry_out;
   uint32_t* const carry = kFix ? nullptr : a.carry;
-  const uint32_t hot_log2 = kFix ? 0u : a.hot_log2;
+  const uint32_t hot_log2 = kRs ? 0u : a.hot_log2;
   const uint32_t* const dmap = kFix ? nullptr : a.dmap;
   const uint32_t first_runs = kFix ? 0u : a.first_runs;
-  unsigned long long* const list_out = kFix ? nullptr : a.list_out;
+  unsigned long long* const list_out = kRs ? nullptr : a.list_out;
   const bool seq_mode = kFix || a.count_mode == IG_COUNT_ONCE_PER_SEQUENCE;
   const uint32_t set_max_windows = kFix ? 0u : a.set_max_windows;
   const uint32_t prefetch_tiles = kFix ? 0u : a.prefetch_tiles;
@@ -1227,25 +1229,29 @@ __global__ void __launch_bounds__(1024) scan_kernel(const ScanArgs a) {
   scan_body<SB, BASE, 0>(a);
 }
 
-// The candidate scan of byte corpora in the configuration of the rank/select
-// passes - prefix ids by DEPTH rank/select levels, Eq. 2 with the set and
-// spill lists, 16-bit counters, survivors not listed - with the switches of
-// every other configuration fixed at compile time (the same code, fewer
-// branches and live values).
-template <uint32_t DEPTH>
+// Scans of byte corpora under Eq. 2 with the set and spill lists and 16-bit
+// counters, with the switches of every other configuration fixed at compile
+// time (the same code, fewer branches and live values): scan_rs_kernel<1|2>
+// for candidate passes with prefix ids by one or two rank/select levels,
+// scan_rs_kernel<3> for candidate passes with the probe table,
+// scan_base_kernel for the base pass.
+template <uint32_t V>
 __global__ void __launch_bounds__(1024) scan_rs_kernel(const ScanArgs a) {
-  scan_body<8, false, DEPTH>(a);
+  scan_body<8, false, V>(a);
+}
+__global__ void __launch_bounds__(1024) scan_base_kernel(const ScanArgs a) {
+  scan_body<8, true, 3>(a);
 }
 
-// The depth of the scan_rs_kernel that stands in for scan_kernel with these
-// arguments (0 = none: the general kernel runs).
-uint32_t rs_variant(const ScanArgs& a, uint32_t symbol_bits, bool base_pass) {
-  if (a.general_only || symbol_bits != 8 || base_pass || a.rs_depth < 1 || a.rs_depth > 2 || a.carry ||
-      a.hot_log2 || a.dmap || a.first_runs || a.list_out || a.rlog || a.bitmap || a.gset || !a.narrow ||
-      a.check_overflow || a.count_mode != IG_COUNT_ONCE_PER_SEQUENCE || !a.spill || a.set_max_windows ||
-      a.prefetch_tiles)
+// The variant that stands in for scan_kernel with these arguments (0 =
+// none: the general kernel runs; 1..3 as scan_body's V).
+uint32_t scan_variant(const ScanArgs& a, uint32_t symbol_bits, bool base_pass) {
+  if (a.general_only || symbol_bits != 8 || a.carry || a.dmap || a.first_runs || a.rlog || a.bitmap || a.gset ||
+      !a.narrow || a.check_overflow || a.count_mode != IG_COUNT_ONCE_PER_SEQUENCE || !a.spill ||
+      a.set_max_windows || a.prefetch_tiles)
     return 0;
-  return a.rs_depth;
+  if (base_pass || a.rs_depth == 0) return 3;
+  return (a.rs_depth <= 2 && !a.hot_log2 && !a.list_out) ? a.rs_depth : 0;
 }
 
 template <int SB>
@@ -1455,11 +1461,15 @@ void* pick(uint32_t symbol_bits, bool base_pass) {
 }  // namespace
 
 cudaError_t scan_set_smem_limit(uint32_t symbol_bits, bool base_pass, size_t smem) {
-  if (symbol_bits == 8 && !base_pass)
-    for (void* f : {reinterpret_cast<void*>(scan_rs_kernel<1>), reinterpret_cast<void*>(scan_rs_kernel<2>)}) {
+  if (symbol_bits == 8) {
+    void* const rs[] = {reinterpret_cast<void*>(scan_rs_kernel<1>), reinterpret_cast<void*>(scan_rs_kernel<2>),
+                        reinterpret_cast<void*>(scan_rs_kernel<3>)};
+    void* const bs[] = {reinterpret_cast<void*>(scan_base_kernel)};
+    for (void* f : base_pass ? std::vector<void*>(bs, bs + 1) : std::vector<void*>(rs, rs + 3)) {
       const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
+  }
   return cudaFuncSetAttribute(pick(symbol_bits, base_pass), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
@@ -1497,9 +1507,11 @@ void launch_log_count(const ScanArgs& a, cudaStream_t s) {
 void launch_scan(const ScanArgs& a, uint32_t symbol_bits, bool base_pass, int grid, int threads,
                  size_t smem, cudaStream_t s) {
   if (symbol_bits == 8) {
-    const uint32_t rs = rs_variant(a, symbol_bits, base_pass);
-    if (rs == 1) scan_rs_kernel<1><<<grid, threads, smem, s>>>(a);
-    else if (rs == 2) scan_rs_kernel<2><<<grid, threads, smem, s>>>(a);
+    const uint32_t v = scan_variant(a, symbol_bits, base_pass);
+    if (v && base_pass) scan_base_kernel<<<grid, threads, smem, s>>>(a);
+    else if (v == 1) scan_rs_kernel<1><<<grid, threads, smem, s>>>(a);
+    else if (v == 2) scan_rs_kernel<2><<<grid, threads, smem, s>>>(a);
+    else if (v == 3) scan_rs_kernel<3><<<grid, threads, smem, s>>>(a);
     else if (base_pass) scan_kernel<8, true><<<grid, threads, smem, s>>>(a);
     else scan_kernel<8, false><<<grid, threads, smem, s>>>(a);
   } else {
