@@ -494,7 +494,7 @@ def main(argv=None):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "scan_kernel (corpus scan of one pass)",
+                     "kernel": "corpus scan of one pass (scan_kernel and its compiled variants, chain_kernel)",
                      "peak_kind": f"{peak_kind} hbm_gbs", "avg_scan_ms": avg_scan_s * 1e3,
                      "scan_ms_per_pass": per_pass_median(scan_ms, npass),
                      "pass_ms_per_pass": per_pass_median([x for r in pass_ms for x in r], npass)},
