@@ -10,6 +10,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -208,6 +209,23 @@ struct ig_plan {
 };
 
 namespace {
+
+// The scan kernels' dynamic shared-memory limits belong to the kernels, so
+// every plan of the process shares them: each plan sets them to the largest
+// size any plan has needed (per alphabet width and kernel group), never
+// lowering them under a live plan made with larger tiles or sets.
+cudaError_t set_shared_limits(uint32_t sb, size_t base_smem, size_t scan_smem) {
+  static std::mutex mu;
+  static size_t most[2][2] = {{0, 0}, {0, 0}};  // [sb == 8][base pass, candidate and chain passes]
+  std::lock_guard<std::mutex> lock(mu);
+  size_t* m = most[sb == 8 ? 1 : 0];
+  m[0] = std::max(m[0], base_smem);
+  m[1] = std::max(m[1], scan_smem);
+  cudaError_t e = scan_set_smem_limit(sb, true, m[0]);
+  if (e == cudaSuccess) e = scan_set_smem_limit(sb, false, m[1]);
+  if (e == cudaSuccess) e = chain_set_smem_limit(sb, m[1]);
+  return e;
+}
 
 // Every device allocation of a plan goes through here: counted, skipped in a
 // dry run, stream-ordered with IG_F_ASYNC_ALLOC.
@@ -863,9 +881,7 @@ ig_status intergrams_plan(const ig_params* p, const void* data, const uint64_t* 
       pl->base_smem += (size_t)4 * pl->base_tile_words;
     }
   }
-  PLAN_CUDA(scan_set_smem_limit(pl->sb, true, pl->base_smem));
-  PLAN_CUDA(scan_set_smem_limit(pl->sb, false, pl->scan_smem));
-  PLAN_CUDA(chain_set_smem_limit(pl->sb, pl->scan_smem));
+  PLAN_CUDA(set_shared_limits(pl->sb, pl->base_smem, pl->scan_smem));
   pl->tile_windows = (uint32_t)tile_windows;
   pl->runs_per_tile = (uint32_t)((tile_windows + kRunChunk - 1) / kRunChunk);
   int occ = std::min(scan_max_ctas_per_sm(pl->sb, false, pl->scan_threads, pl->scan_smem),

@@ -126,6 +126,25 @@ def test_results_do_not_depend_on_tuning(tuning):
     check_all_passes(data, off, n=5, k=700, Z=3000, base_n=2, tuning=tuning)
 
 
+def test_plans_with_different_shared_memory_coexist():
+    """The scan kernels' shared-memory limits belong to the kernels, not to a
+    plan: a plan made later with small tiles and sets must leave a live plan
+    that needs more shared memory runnable, and both stay bit-exact."""
+    data, off, _ = synth.make_corpus("markov_2mb", m=16, seed=12)
+    big = dict(threads=1024, words_per_thread=7, smem_set_log2=14, ctas_per_sm=1, dedupe_bitmap=1)
+    small = dict(threads=256, words_per_thread=1, smem_set_log2=8, ctas_per_sm=4, dedupe_bitmap=1)
+    ek, ec = O.intergrams(data, off, 5, 100, 400, base_n=2)
+    d, o = dev(data, off)
+    plans = [B.Plan(d, o, n=5, k=100, candidates=400, base_n=2, tuning=t) for t in (big, small)]
+    for pl in plans:  # the large plan runs after the small one was made
+        pl.run()
+        gk, gc, gj = pl.topk()
+        assert gj == 5
+        assert np.array_equal(gc, ec) and np.array_equal(gk, ek)
+    for pl in plans:
+        pl.close()
+
+
 def check_passes(data, off, *, n, k, Z, base_n, js, mode=0, symbol_bits=8, tuning=None):
     """Run every pass; compare with the oracle after the passes in `js`."""
     expect = {}
