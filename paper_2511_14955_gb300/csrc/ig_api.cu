@@ -1413,7 +1413,9 @@ ig_status intergrams_features(ig_plan* pl, uint64_t* row_ptr, uint32_t* cols, ui
   if (cols && pl->feat_total) {
     uint32_t* d_cols = nullptr;
     IG_CUDA(device_malloc(reinterpret_cast<void**>(&d_cols), sizeof(uint32_t) * pl->feat_total, false, s));
-    cudaError_t e = cudaMemsetAsync(pl->feat_q + 1, 0, sizeof(uint32_t), s);
+    // the limit again: another plan's feature call since the counting scan may have changed it
+    cudaError_t e = feature_set_smem(pl->sb, fsmem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->feat_q + 1, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) {
       launch_features(pl->data, pl->data_bytes, pl->offsets, pl->d_order, pl->m, pl->p.n, pl->sb, pl->out_keys,
                       pl->feat_rows, rb, pl->feat_keys, pl->feat_table, pl->feat_table_log2, pl->feat_q, pl->feat_q + 2,
