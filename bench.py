@@ -206,7 +206,7 @@ def _oracle_run(name, seed, p, nbytes, workers):
     size = int(data.size)
     sample = (f"first {keep} sequences of {name} (seed {seed}, {size / 1e6:.1f} MB), full job n={p['n']} "
               f"k={p['k']} Z={p['candidates']} base_n={p['base_n']}, {dt:.1f} s on {workers} core(s)")
-    return size * passes_of(p) / dt / 1e9, sample
+    return size * passes_of(p) / dt / 1e9, sample, dt
 
 
 def cpu_baseline(name: str, seed: int, p, all_bytes: int, single_bytes: int):
@@ -216,8 +216,8 @@ def cpu_baseline(name: str, seed: int, p, all_bytes: int, single_bytes: int):
     single-threaded oracle), each on a bounded sample of the same seeded
     workload with the same parameters."""
     cores = os.cpu_count() or 1
-    value, sample = _oracle_run(name, seed, p, all_bytes, cores)
-    single, single_sample = _oracle_run(name, seed, p, single_bytes, 1)
+    value, sample, _ = _oracle_run(name, seed, p, all_bytes, cores)
+    single, single_sample, _ = _oracle_run(name, seed, p, single_bytes, 1)
     return {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample,
             "single_core": {"value": single, "unit": "GB/s", "cores": 1, "sample": single_sample}}
 
@@ -326,16 +326,19 @@ def run_reference(args):
     p = job_params(args.workload)
     p["count_mode"] = args.count_mode
     cores = os.cpu_count() or 1
-    vals, sample = [], ""
+    vals, secs, sample = [], [], ""
     for i in range(args.warmup + args.steps):
-        v, sample = _oracle_run(args.workload, args.seed, p, int(args.ref_mb * 1e6), cores)
+        v, sample, dt = _oracle_run(args.workload, args.seed, p, int(args.ref_mb * 1e6), cores)
         if i >= args.warmup:
             vals.append(v)
+            secs.append(dt)
     value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": "scanned GB/s per pass (n=8,k=64K)", "value": value, "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": statistics.median(secs) * 1e3 if secs else None,
+        "ms_per_step_covers": "one step = the whole job on the bounded sample named in cpu_baseline",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, **p},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
