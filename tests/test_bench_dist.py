@@ -51,3 +51,4 @@ def test_reference_arm_prints_one_line(capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
+    assert line["ms_per_step"] > 0 and line["higher_is_better"] is True
